@@ -1,0 +1,183 @@
+/*
+ * dctplus.h — C ABI of the GB300 Fast DCT+ library.
+ *
+ * The transform: for the path graph Laplacian L~ = U diag(lambda) U^T and a
+ * rank-one update L = L~ + rho v v^T (Def. 2.3) with eigenbasis X, a signal
+ * x in R^n maps to its GFT coefficients y = X^T x. Theorem 3.1 (eq. fwd_map)
+ * factors this as
+ *     y = -diag(a) C(mu, lambda) diag(z) U^T x,
+ * with U^T x the orthonormal DCT-II, z = U^T v, C_ij = 1 / (mu_i - lambda_j)
+ * (Def. 2.1), mu the roots of the secular equation
+ * 1 + rho sum_j z_j^2 / (lambda_j - mu) = 0 (Remark on the setup stage), and
+ * a the column normalisation. Algorithm 1 gives the forward steps: DCT-II,
+ * scale by z, Cauchy product, scale by a.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Sizes are in elements. Signals are rows: signal b occupies
+ *   x[b * ldx + 0 .. b * ldx + n - 1]; outputs likewise with ldy.
+ * - Output row order: coefficient i of a signal belongs to the i-th smallest
+ *   eigenvalue of L. Eigenvector signs follow the rule <u_pi(i), x_i> > 0
+ *   (pi pairs the i-th non-deflated root with the i-th non-deflated pole in
+ *   ascending order; a deflated eigenvector u_j keeps its DCT sign). With
+ *   rho = 0 the transform is exactly the orthonormal DCT-II.
+ * - Ownership: the caller owns every buffer passed in. A plan owns its own
+ *   device tables (a few n-vectors, plus at most O(n^2) floats for n <= 4096)
+ *   and frees them in dctplus_destroy.
+ * - Streams: execute calls are asynchronous on the given stream (0 = legacy
+ *   default stream), never synchronise, and only read the plan, so one plan may
+ *   be executed concurrently on several streams. Plans are immutable after
+ *   creation.
+ * - Errors: every call returns a dctplus_status and never throws. Argument
+ *   errors are detected on the host before any launch. Device-side checks
+ *   (index guards) write a device error word, read by dctplus_sync_check.
+ * - Device: a plan lives on the device that was current at dctplus_plan
+ *   (or opts->device); execute calls must be issued with that device current.
+ */
+#ifndef DCTPLUS_H
+#define DCTPLUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dctplus_plan_s* dctplus_plan_t;
+typedef struct dctplus_group_s* dctplus_group_t;
+typedef struct CUstream_st* dctplus_stream_t; /* same handle as cudaStream_t */
+
+typedef enum {
+    DCTPLUS_OK = 0,
+    DCTPLUS_ERR_INVALID_ARG = 1,   /* bad size, pointer, stride or non-finite input */
+    DCTPLUS_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+    DCTPLUS_ERR_NOT_CONVERGED = 3, /* secular root iteration hit its cap */
+    DCTPLUS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    DCTPLUS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    DCTPLUS_ERR_DEVICE_CHECK = 6,  /* a device-side guard recorded a violation */
+    DCTPLUS_ERR_NO_DEVICE = 7      /* no CUDA device is visible */
+} dctplus_status;
+
+typedef enum { DCTPLUS_F32 = 0, DCTPLUS_F64 = 1 } dctplus_dtype;
+
+/* How the Cauchy product of Theorem 3.1 is evaluated for FP32 data. */
+typedef enum {
+    DCTPLUS_CAUCHY_AUTO = 0,  /* pick by n (tuned crossover) */
+    DCTPLUS_CAUCHY_DENSE = 1, /* dense product, Cauchy tiles generated on chip */
+    DCTPLUS_CAUCHY_HIER = 2,  /* O(n log n) hierarchical far-field expansion (Theorem 3.2) */
+    DCTPLUS_CAUCHY_SIMT = 3   /* plain CUDA-core product from a stored FP32 table (n <= 4096) */
+} dctplus_cauchy_mode;
+
+typedef struct {
+    int cauchy_mode;      /* dctplus_cauchy_mode; 0 = auto */
+    int max_secular_iter; /* cap on root iterations per root; 0 = 200 */
+    int hier_rank;        /* far-field expansion order; 0 = default (16) */
+    int device;           /* CUDA device ordinal; -1 = current device */
+} dctplus_opts;
+
+/* ------------------------------------------------------------------ plans */
+
+/* Setup stage (Remark in Sec. 3): computes lambda (closed form), z = U^T v,
+ * deflation of z_j ~ 0 (Sec. 4), the secular roots mu inside the Lemma 4.1
+ * brackets (FP64, on the GPU) stored as nearest pole + offset, and the
+ * normalisation a, then uploads the tables the execute kernels read.
+ *   out   : receives the plan handle (owned by the library).
+ *   n     : signal length, 2 <= n <= 16384.
+ *   v_host: n doubles in host memory (copied; need not outlive the call).
+ *   rho   : update weight; 0 gives the plain DCT-II. Must be finite.
+ *   opts  : NULL for defaults.
+ * Synchronous. Errors: INVALID_ARG (n out of range, NULL pointers, non-finite
+ * v or rho), NOT_CONVERGED, CUDA, NO_DEVICE. On error *out is NULL. */
+dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, double rho,
+                            const dctplus_opts* opts);
+
+void dctplus_destroy(dctplus_plan_t plan);
+
+/* Plan inspection (host copies of the FP64 setup quantities), for checking
+ * the setup stage against Lemma 4.1 and the secular equation.
+ *   eigenvalues: n doubles, ascending eigenvalues of L (output row order).
+ *   z          : n doubles, z = U^T v.
+ *   row_kind   : n ints, 1 = secular-root row, 0 = deflated row.
+ *   row_pole   : n ints, the origin pole index of the row (deflated: its own j).
+ *   row_tau    : n doubles, eigenvalue - lambda[row_pole].
+ *   row_a      : n doubles, a_i of Theorem 3.1 (0 for deflated rows).
+ * Any output pointer may be NULL. */
+dctplus_status dctplus_plan_inspect(dctplus_plan_t plan, double* eigenvalues, double* z,
+                                    int* row_kind, int* row_pole, double* row_tau,
+                                    double* row_a);
+
+/* Returns n, or -1 for a NULL plan. */
+int dctplus_plan_size(dctplus_plan_t plan);
+
+/* The Cauchy evaluation the plan uses for FP32 execute (a dctplus_cauchy_mode). */
+int dctplus_plan_cauchy_mode(dctplus_plan_t plan);
+
+/* --------------------------------------------------------------- forward */
+
+/* Forward transform of a batch (Algorithm 1; Theorem 3.1 eq. fwd_map):
+ * y_b = X^T x_b for b = 0..batch-1.
+ *   dtype : DCTPLUS_F32 (split-TF32 tensor-core contractions, FP32 in/out) or
+ *           DCTPLUS_F64 (FP64 CUDA-core path, n <= 1024).
+ *   x_dev, y_dev: device pointers, 16-byte aligned, rows of n elements with
+ *           leading dimensions ldx, ldy >= n (multiples of 4 for F32, 2 for F64).
+ *           x and y must not overlap.
+ *   batch : number of signals, >= 0 (0 is a no-op).
+ * Asynchronous on `stream`. Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const void* x_dev,
+                               int64_t ldx, void* y_dev, int64_t ldy, int64_t batch,
+                               dctplus_stream_t stream);
+
+/* Same transform with HOST buffers: copies x to the device, transforms, copies
+ * y back, all on `stream`, and returns after the stream has finished. Pinned
+ * host memory gives full copy bandwidth. Uses a device staging buffer owned by
+ * the plan (grown on demand), so calls on one plan must not overlap. */
+dctplus_status dctplus_execute_host(dctplus_plan_t plan, dctplus_dtype dtype, const void* x_host,
+                                    void* y_host, int64_t batch, dctplus_stream_t stream);
+
+/* ------------------------------------------------- mixed-size batches (FP32) */
+
+/* A group of plans with n <= 64 executed together in one persistent launch:
+ * each segment of the input names one plan. `plans` are borrowed (must outlive
+ * the group). All plans must live on the same device. */
+dctplus_status dctplus_group_create(dctplus_group_t* out, int count, const dctplus_plan_t* plans);
+void dctplus_group_destroy(dctplus_group_t group);
+
+/* Segment descriptor: three int64 per segment, {plan index in the group,
+ * element offset of the segment's first sample in x and y, number of rows}.
+ * A segment's rows are contiguous (stride = n of its plan); offsets must be
+ * multiples of 4 elements. */
+#define DCTPLUS_SEG_WORDS 3
+
+/* Forward transform of every segment in one launch (CUDA-graph capturable).
+ *   x_dev, y_dev : FP32 device buffers holding all segments.
+ *   seg_host     : nseg * 3 int64 in host memory (validated, then uploaded
+ *                  into a group-owned device table; the upload is a
+ *                  host-to-device copy on `stream` when the table changes).
+ * Errors: INVALID_ARG, UNSUPPORTED (a plan with n > 64), CUDA. */
+dctplus_status dctplus_execute_group(dctplus_group_t group, const float* x_dev, float* y_dev,
+                                     const int64_t* seg_host, int nseg, dctplus_stream_t stream);
+
+/* Host-buffer variant of dctplus_execute_group (copies inside, synchronous).
+ * total_elems = size of x_host and y_host in floats. */
+dctplus_status dctplus_execute_group_host(dctplus_group_t group, const float* x_host,
+                                          float* y_host, int64_t total_elems,
+                                          const int64_t* seg_host, int nseg,
+                                          dctplus_stream_t stream);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* Synchronises `stream`, then reads and clears the device error word.
+ * Returns DCTPLUS_OK, DCTPLUS_ERR_DEVICE_CHECK or DCTPLUS_ERR_TIMEOUT. */
+dctplus_status dctplus_sync_check(dctplus_stream_t stream);
+
+/* Number of kernels this library has launched in this process (all devices). */
+int64_t dctplus_launch_count(void);
+
+const char* dctplus_status_string(dctplus_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCTPLUS_H */

@@ -61,9 +61,13 @@ class CauchyPlan:
         return self.lam[self.origin] + self.tau
 
 
-def _secular_g(n, rho, z_nd, poles, origin, tau):
-    """g(mu) = 1/rho + sum_j z_j^2/(lambda_j - mu) for mu = lambda_origin + tau (vectorised)."""
-    d = pole_differences(n, poles[None, :], origin[:, None])  # lambda_j - lambda_origin
+def _secular_g(n, rho, z_nd, poles, origin, tau, d=None):
+    """g(mu) = 1/rho + sum_j z_j^2/(lambda_j - mu) for mu = lambda_origin + tau (vectorised).
+
+    ``d`` may pass the precomputed lambda_j - lambda_origin matrix.
+    """
+    if d is None:
+        d = pole_differences(n, poles[None, :], origin[:, None])  # lambda_j - lambda_origin
     return 1.0 / rho + np.sum(z_nd[None, :] ** 2 / (d - tau[:, None]), axis=1)
 
 
@@ -71,6 +75,7 @@ def _bisect(n, rho, z_nd, poles, origin, lo, hi, max_iter=4000):
     """Bisection on tau in (lo, hi) with g(lo) < 0 <= g(hi); stops when no midpoint is left."""
     lo = lo.copy()
     hi = hi.copy()
+    d_all = pole_differences(n, poles[None, :], origin[:, None])  # fixed over the iteration
     active = np.ones(lo.shape, dtype=bool)
     for _ in range(max_iter):
         if not active.any():
@@ -82,7 +87,7 @@ def _bisect(n, rho, z_nd, poles, origin, lo, hi, max_iter=4000):
         idx, mid = idx[~done], mid[~done]
         if idx.size == 0:
             break
-        g = _secular_g(n, rho, z_nd, poles, origin[idx], mid)
+        g = _secular_g(n, rho, z_nd, poles, origin[idx], mid, d=d_all[idx])
         up = g >= 0.0
         hi[idx[up]] = mid[up]
         lo[idx[~up]] = mid[~up]
@@ -90,8 +95,8 @@ def _bisect(n, rho, z_nd, poles, origin, lo, hi, max_iter=4000):
         raise RuntimeError("secular bisection did not converge")
     # return the end of the final bracket with the smaller |g| (lo may sit on a pole)
     with np.errstate(divide="ignore", invalid="ignore"):
-        glo = np.abs(_secular_g(n, rho, z_nd, poles, origin, lo))
-        ghi = np.abs(_secular_g(n, rho, z_nd, poles, origin, hi))
+        glo = np.abs(_secular_g(n, rho, z_nd, poles, origin, lo, d=d_all))
+        ghi = np.abs(_secular_g(n, rho, z_nd, poles, origin, hi, d=d_all))
     glo = np.where(np.isfinite(glo), glo, np.inf)
     return np.where(ghi <= glo, hi, lo)
 

@@ -1,0 +1,207 @@
+"""GB300 Fast DCT+: batched GFTs of rank-one updates of the path graph.
+
+Python layer over the C ABI in ``include/dctplus.h``. Functions named
+``dctplus_*`` mirror the C entry points one to one (handles and raw pointers);
+``Plan`` and ``Group`` wrap them for torch tensors. PyTorch supplies device
+memory and streams only: every step of the transform runs in the library's
+CUDA kernels, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    CAUCHY_AUTO, CAUCHY_DENSE, CAUCHY_HIER, CAUCHY_SIMT, F32, F64, SEG_WORDS, DctPlusError, Opts,
+    check,
+)
+
+__all__ = [
+    "Plan", "Group", "DctPlusError", "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect",
+    "dctplus_execute", "dctplus_execute_host", "dctplus_group_create", "dctplus_group_destroy",
+    "dctplus_execute_group", "dctplus_execute_group_host", "dctplus_sync_check",
+    "dctplus_launch_count", "dctplus_status_string", "library_path",
+]
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- raw C names
+
+def dctplus_status_string(status: int) -> str:
+    return _lib.load().dctplus_status_string(int(status)).decode()
+
+
+def dctplus_launch_count() -> int:
+    return int(_lib.load().dctplus_launch_count())
+
+
+def dctplus_plan(n: int, v, rho: float, opts: Opts | None = None) -> ctypes.c_void_p:
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    if v.shape != (n,):
+        raise ValueError("v must have shape (n,)")
+    h = ctypes.c_void_p()
+    st = _lib.load().dctplus_plan(ctypes.byref(h), int(n), v.ctypes.data, float(rho),
+                                  ctypes.byref(opts) if opts is not None else None)
+    check(st, "dctplus_plan")
+    return h
+
+
+def dctplus_destroy(handle) -> None:
+    _lib.load().dctplus_destroy(handle)
+
+
+def dctplus_plan_inspect(handle, n: int) -> dict:
+    out = {k: np.zeros(n) for k in ("eigenvalues", "z", "row_tau", "row_a")}
+    out["row_kind"] = np.zeros(n, dtype=np.int32)
+    out["row_pole"] = np.zeros(n, dtype=np.int32)
+    st = _lib.load().dctplus_plan_inspect(
+        handle, out["eigenvalues"].ctypes.data, out["z"].ctypes.data, out["row_kind"].ctypes.data,
+        out["row_pole"].ctypes.data, out["row_tau"].ctypes.data, out["row_a"].ctypes.data)
+    check(st, "dctplus_plan_inspect")
+    return out
+
+
+def dctplus_execute(handle, dtype: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, batch: int,
+                    stream: int) -> None:
+    st = _lib.load().dctplus_execute(handle, int(dtype), x_ptr, int(ldx), y_ptr, int(ldy),
+                                     int(batch), stream)
+    check(st, "dctplus_execute")
+
+
+def dctplus_execute_host(handle, dtype: int, x_ptr: int, y_ptr: int, batch: int, stream: int) -> None:
+    st = _lib.load().dctplus_execute_host(handle, int(dtype), x_ptr, y_ptr, int(batch), stream)
+    check(st, "dctplus_execute_host")
+
+
+def dctplus_group_create(handles) -> ctypes.c_void_p:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    g = ctypes.c_void_p()
+    check(_lib.load().dctplus_group_create(ctypes.byref(g), len(handles), arr), "dctplus_group_create")
+    return g
+
+
+def dctplus_group_destroy(g) -> None:
+    _lib.load().dctplus_group_destroy(g)
+
+
+def dctplus_execute_group(g, x_ptr: int, y_ptr: int, seg: np.ndarray, stream: int) -> None:
+    seg = np.ascontiguousarray(seg, dtype=np.int64).reshape(-1, SEG_WORDS)
+    st = _lib.load().dctplus_execute_group(g, x_ptr, y_ptr, seg.ctypes.data, seg.shape[0], stream)
+    check(st, "dctplus_execute_group")
+
+
+def dctplus_execute_group_host(g, x_ptr: int, y_ptr: int, total_elems: int, seg: np.ndarray,
+                               stream: int) -> None:
+    seg = np.ascontiguousarray(seg, dtype=np.int64).reshape(-1, SEG_WORDS)
+    st = _lib.load().dctplus_execute_group_host(g, x_ptr, y_ptr, int(total_elems), seg.ctypes.data,
+                                                seg.shape[0], stream)
+    check(st, "dctplus_execute_group_host")
+
+
+def dctplus_sync_check(stream: int = 0) -> int:
+    return int(_lib.load().dctplus_sync_check(stream))
+
+
+# ---------------------------------------------------------------- wrappers
+
+class Plan:
+    """A Fast DCT+ plan: the GFT of L~ + rho v v^T for signals of length n."""
+
+    def __init__(self, n: int, v, rho: float, cauchy_mode: int = CAUCHY_AUTO,
+                 max_secular_iter: int = 0, hier_rank: int = 0, device: int = -1):
+        self.n = int(n)
+        self.rho = float(rho)
+        opts = Opts(cauchy_mode, max_secular_iter, hier_rank, device)
+        self.handle = dctplus_plan(self.n, v, self.rho, opts)
+
+    @property
+    def cauchy_mode(self) -> int:
+        return int(_lib.load().dctplus_plan_cauchy_mode(self.handle))
+
+    def inspect(self) -> dict:
+        return dctplus_plan_inspect(self.handle, self.n)
+
+    def forward(self, x, out=None, stream=None):
+        """y = X^T x for every row of a CUDA tensor x of shape (batch, n), float32 or float64."""
+        import torch
+        if x.dim() != 2 or x.shape[1] != self.n or x.stride(1) != 1:
+            raise ValueError("x must be (batch, n) with unit stride along n")
+        dtype = {torch.float32: F32, torch.float64: F64}.get(x.dtype)
+        if dtype is None:
+            raise TypeError("x must be float32 or float64")
+        if out is None:
+            out = torch.empty_like(x, memory_format=torch.contiguous_format)
+        dctplus_execute(self.handle, dtype, x.data_ptr(), x.stride(0), out.data_ptr(),
+                        out.stride(0), x.shape[0], _stream_handle(stream))
+        return out
+
+    def forward_host(self, x: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Same transform on host arrays (copies to and from the GPU inside the call)."""
+        x = np.ascontiguousarray(x)
+        dtype = {np.dtype(np.float32): F32, np.dtype(np.float64): F64}[x.dtype]
+        if out is None:
+            out = np.empty_like(x)
+        dctplus_execute_host(self.handle, dtype, x.ctypes.data, out.ctypes.data, x.shape[0],
+                             _stream_handle(stream) if stream is not None else 0)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            dctplus_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Several plans with n <= 64 run as one persistent launch over segments."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self.handle = dctplus_group_create([p.handle for p in self.plans])
+
+    def forward(self, x, seg: np.ndarray, out=None, stream=None):
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError("x must be a contiguous float32 CUDA tensor")
+        if out is None:
+            out = torch.empty_like(x)
+        dctplus_execute_group(self.handle, x.data_ptr(), out.data_ptr(), seg, _stream_handle(stream))
+        return out
+
+    def forward_host(self, x: np.ndarray, seg: np.ndarray, out=None, stream=None) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        if out is None:
+            out = np.empty_like(x)
+        dctplus_execute_group_host(self.handle, x.ctypes.data, out.ctypes.data, x.size, seg,
+                                   _stream_handle(stream) if stream is not None else 0)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            dctplus_group_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

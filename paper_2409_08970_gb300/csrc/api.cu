@@ -1,0 +1,354 @@
+// C ABI entry points: argument checks, plan lifetime, dispatch to kernels.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "internal.cuh"
+
+namespace dctplus {
+
+dctplus_status launch_small_tc(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
+                               int64_t ldy, int64_t batch, cudaStream_t s);  // small_tc.cu
+bool small_tc_available(dctplus_plan_t p);                                   // small_tc.cu
+dctplus_status group_prepare(dctplus_group_t g, const int64_t* seg_host, int nseg,
+                             cudaStream_t s);                                // small_simt.cu
+dctplus_status group_upload_plans(dctplus_group_t g);                        // small_simt.cu
+dctplus_status launch_group_simt(dctplus_group_t g, const float* x, float* y, cudaStream_t s);
+dctplus_status launch_group_tc(dctplus_group_t g, const float* x, float* y, cudaStream_t s);
+bool group_tc_available(dctplus_group_t g);
+
+static std::mutex g_err_mu;
+static unsigned* g_err_words[64] = {};
+
+unsigned* device_error_word(int device) {
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    if (!g_err_words[device]) {
+        unsigned* w = nullptr;
+        if (cudaMalloc((void**)&w, sizeof(unsigned)) != cudaSuccess) return nullptr;
+        cudaMemset(w, 0, sizeof(unsigned));
+        g_err_words[device] = w;
+    }
+    return g_err_words[device];
+}
+
+// Per-(plan, stream) scratch, grown on demand. The first call on a stream
+// allocates, so it must precede any stream capture.
+struct Workspace {
+    cudaStream_t stream;
+    void* ptr;
+    size_t bytes;
+};
+static std::mutex g_ws_mu;
+
+struct PlanWs {
+    dctplus_plan_t plan;
+    std::vector<Workspace> ws;
+};
+static std::vector<PlanWs> g_ws;
+
+void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    PlanWs* pw = nullptr;
+    for (auto& e : g_ws)
+        if (e.plan == p) pw = &e;
+    if (!pw) { g_ws.push_back({p, {}}); pw = &g_ws.back(); }
+    for (auto& w : pw->ws) {
+        if (w.stream != st) continue;
+        if (w.bytes >= bytes) return w.ptr;
+        cudaStreamSynchronize(st);
+        cudaFree(w.ptr);
+        w.ptr = nullptr;
+        if (cudaMalloc(&w.ptr, bytes) != cudaSuccess) { w.bytes = 0; return nullptr; }
+        w.bytes = bytes;
+        return w.ptr;
+    }
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(bytes, 256)) != cudaSuccess) return nullptr;
+    pw->ws.push_back({st, q, std::max<size_t>(bytes, 256)});
+    return q;
+}
+
+static void release_workspaces(dctplus_plan_t p) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (size_t i = 0; i < g_ws.size(); ++i) {
+        if (g_ws[i].plan != p) continue;
+        for (auto& w : g_ws[i].ws) cudaFree(w.ptr);
+        g_ws.erase(g_ws.begin() + i);
+        return;
+    }
+}
+
+static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+static dctplus_status check_device(int want) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return DCTPLUS_ERR_NO_DEVICE;
+    return cur == want ? DCTPLUS_OK : DCTPLUS_ERR_INVALID_ARG;
+}
+
+}  // namespace dctplus
+
+using namespace dctplus;
+
+extern "C" {
+
+const char* dctplus_status_string(dctplus_status s) {
+    switch (s) {
+        case DCTPLUS_OK: return "ok";
+        case DCTPLUS_ERR_INVALID_ARG: return "invalid argument";
+        case DCTPLUS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case DCTPLUS_ERR_NOT_CONVERGED: return "secular root iteration did not converge";
+        case DCTPLUS_ERR_CUDA: return "CUDA runtime error";
+        case DCTPLUS_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DCTPLUS_ERR_DEVICE_CHECK: return "device-side check failed";
+        case DCTPLUS_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+int64_t dctplus_launch_count(void) { return g_launches.load(); }
+
+dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, double rho,
+                            const dctplus_opts* opts) {
+    if (!out) return DCTPLUS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!v_host || n < 2 || n > kMaxN || !std::isfinite(rho)) return DCTPLUS_ERR_INVALID_ARG;
+    for (int j = 0; j < n; ++j)
+        if (!std::isfinite(v_host[j])) return DCTPLUS_ERR_INVALID_ARG;
+    dctplus_opts o{};
+    o.device = -1;
+    if (opts) o = *opts;
+    if (o.cauchy_mode < 0 || o.cauchy_mode > DCTPLUS_CAUCHY_SIMT || o.max_secular_iter < 0)
+        return DCTPLUS_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DCTPLUS_ERR_NO_DEVICE;
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) return DCTPLUS_ERR_NO_DEVICE;
+    } else {
+        if (dev >= ndev) return DCTPLUS_ERR_INVALID_ARG;
+        if (cudaSetDevice(dev) != cudaSuccess) return DCTPLUS_ERR_CUDA;
+    }
+    dctplus_plan_s* p = new (std::nothrow) dctplus_plan_s();
+    if (!p) return DCTPLUS_ERR_CUDA;
+    p->n = n;
+    p->rho = rho;
+    p->device = dev;
+    p->v.assign(v_host, v_host + n);
+    p->cauchy_mode = o.cauchy_mode;
+    dctplus_status st = build_plan(p, o);
+    if (st != DCTPLUS_OK) {
+        free_plan_tables(p);
+        delete p;
+        return st;
+    }
+    if (p->cauchy_mode == DCTPLUS_CAUCHY_AUTO) p->cauchy_mode = DCTPLUS_CAUCHY_SIMT;
+    *out = p;
+    return DCTPLUS_OK;
+}
+
+void dctplus_destroy(dctplus_plan_t p) {
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    release_workspaces(p);
+    free_plan_tables(p);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+int dctplus_plan_size(dctplus_plan_t p) { return p ? p->n : -1; }
+
+int dctplus_plan_cauchy_mode(dctplus_plan_t p) { return p ? p->cauchy_mode : -1; }
+
+dctplus_status dctplus_plan_inspect(dctplus_plan_t p, double* eigenvalues, double* z,
+                                    int* row_kind, int* row_pole, double* row_tau,
+                                    double* row_a) {
+    if (!p) return DCTPLUS_ERR_INVALID_ARG;
+    size_t n = (size_t)p->n;
+    if (eigenvalues) memcpy(eigenvalues, p->eig.data(), sizeof(double) * n);
+    if (z) memcpy(z, p->z.data(), sizeof(double) * n);
+    if (row_kind) memcpy(row_kind, p->row_kind.data(), sizeof(int) * n);
+    if (row_pole) memcpy(row_pole, p->row_pole.data(), sizeof(int) * n);
+    if (row_tau) memcpy(row_tau, p->row_tau.data(), sizeof(double) * n);
+    if (row_a) memcpy(row_a, p->row_a.data(), sizeof(double) * n);
+    return DCTPLUS_OK;
+}
+
+static dctplus_status check_exec_args(dctplus_plan_t p, dctplus_dtype dtype, const void* x,
+                                      int64_t ldx, const void* y, int64_t ldy, int64_t batch) {
+    if (!p || batch < 0) return DCTPLUS_ERR_INVALID_ARG;
+    if (dtype != DCTPLUS_F32 && dtype != DCTPLUS_F64) return DCTPLUS_ERR_INVALID_ARG;
+    if (batch == 0) return DCTPLUS_OK;
+    if (!x || !y || x == y) return DCTPLUS_ERR_INVALID_ARG;
+    if (ldx < p->n || ldy < p->n) return DCTPLUS_ERR_INVALID_ARG;
+    int q = dtype == DCTPLUS_F32 ? 4 : 2;
+    if (ldx % q || ldy % q || !aligned16(x) || !aligned16(y)) return DCTPLUS_ERR_INVALID_ARG;
+    size_t es = dtype == DCTPLUS_F32 ? 4 : 8;
+    // reject overlapping x / y ranges
+    uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
+    uintptr_t xe = xa + es * (size_t)((batch - 1) * ldx + p->n);
+    uintptr_t ye = ya + es * (size_t)((batch - 1) * ldy + p->n);
+    if (xa < ye && ya < xe) return DCTPLUS_ERR_INVALID_ARG;
+    return DCTPLUS_OK;
+}
+
+dctplus_status dctplus_execute(dctplus_plan_t p, dctplus_dtype dtype, const void* x_dev,
+                               int64_t ldx, void* y_dev, int64_t ldy, int64_t batch,
+                               dctplus_stream_t stream) {
+    dctplus_status st = check_exec_args(p, dtype, x_dev, ldx, y_dev, ldy, batch);
+    if (st != DCTPLUS_OK || batch == 0) return st;
+    if ((st = check_device(p->device)) != DCTPLUS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int n = p->n;
+    if (dtype == DCTPLUS_F64) {
+        if (n > kF64Max) return DCTPLUS_ERR_UNSUPPORTED;
+        if (n > kSmallMax)
+            return launch_dense_f64(p, static_cast<const double*>(x_dev), ldx,
+                                    static_cast<double*>(y_dev), ldy, batch, s);
+        return launch_small_simt_f64(p, static_cast<const double*>(x_dev), ldx,
+                                     static_cast<double*>(y_dev), ldy, batch, s);
+    }
+    const float* x = static_cast<const float*>(x_dev);
+    float* y = static_cast<float*>(y_dev);
+    if (n <= kSmallMax) {
+        if (p->cauchy_mode != DCTPLUS_CAUCHY_SIMT && small_tc_available(p))
+            return launch_small_tc(p, x, ldx, y, ldy, batch, s);
+        return launch_small_simt_f32(p, x, ldx, y, ldy, batch, s);
+    }
+    return launch_large_f32(p, x, ldx, y, ldy, batch, s);
+}
+
+dctplus_status dctplus_execute_host(dctplus_plan_t p, dctplus_dtype dtype, const void* x_host,
+                                    void* y_host, int64_t batch, dctplus_stream_t stream) {
+    if (!p || batch < 0 || (batch > 0 && (!x_host || !y_host))) return DCTPLUS_ERR_INVALID_ARG;
+    if (dtype != DCTPLUS_F32 && dtype != DCTPLUS_F64) return DCTPLUS_ERR_INVALID_ARG;
+    if (batch == 0) return DCTPLUS_OK;
+    dctplus_status st = check_device(p->device);
+    if (st != DCTPLUS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t es = dtype == DCTPLUS_F32 ? 4 : 8;
+    size_t bytes = es * (size_t)batch * p->n;
+    size_t half = (bytes + 255) & ~size_t(255);
+    if (p->stage_bytes < 2 * half) {
+        if (p->d_stage) { cudaStreamSynchronize(s); cudaFree(p->d_stage); p->d_stage = nullptr; }
+        DCTPLUS_CUDA_TRY(cudaMalloc(&p->d_stage, 2 * half));
+        p->stage_bytes = 2 * half;
+    }
+    char* dx = static_cast<char*>(p->d_stage);
+    char* dy = dx + half;
+    DCTPLUS_CUDA_TRY(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, s));
+    st = dctplus_execute(p, dtype, dx, p->n, dy, p->n, batch, stream);
+    if (st != DCTPLUS_OK) return st;
+    DCTPLUS_CUDA_TRY(cudaMemcpyAsync(y_host, dy, bytes, cudaMemcpyDeviceToHost, s));
+    DCTPLUS_CUDA_TRY(cudaStreamSynchronize(s));
+    return DCTPLUS_OK;
+}
+
+dctplus_status dctplus_group_create(dctplus_group_t* out, int count, const dctplus_plan_t* plans) {
+    if (!out) return DCTPLUS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count <= 0 || !plans) return DCTPLUS_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) return DCTPLUS_ERR_INVALID_ARG;
+        if (plans[i]->n > kSmallMax) return DCTPLUS_ERR_UNSUPPORTED;
+        if (plans[i]->device != plans[0]->device) return DCTPLUS_ERR_INVALID_ARG;
+    }
+    dctplus_status st = check_device(plans[0]->device);
+    if (st != DCTPLUS_OK) return st;
+    dctplus_group_s* g = new (std::nothrow) dctplus_group_s();
+    if (!g) return DCTPLUS_ERR_CUDA;
+    g->device = plans[0]->device;
+    g->plans.assign(plans, plans + count);
+    st = group_upload_plans(g);
+    if (st != DCTPLUS_OK) { dctplus_group_destroy(g); return st; }
+    *out = g;
+    return DCTPLUS_OK;
+}
+
+void dctplus_group_destroy(dctplus_group_t g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    if (g->d_plan_tables) cudaFree(g->d_plan_tables);
+    if (g->d_seg) cudaFree(g->d_seg);
+    if (g->d_tiles) cudaFree(g->d_tiles);
+    if (g->d_stage) cudaFree(g->d_stage);
+    delete g;
+}
+
+static dctplus_status check_segments(dctplus_group_t g, const int64_t* seg, int nseg,
+                                     int64_t total_elems) {
+    if (nseg < 0 || (nseg > 0 && !seg)) return DCTPLUS_ERR_INVALID_ARG;
+    for (int s = 0; s < nseg; ++s) {
+        int64_t pi = seg[3 * s], off = seg[3 * s + 1], rows = seg[3 * s + 2];
+        if (pi < 0 || pi >= (int64_t)g->plans.size() || off < 0 || rows < 0 || (off & 3))
+            return DCTPLUS_ERR_INVALID_ARG;
+        if (rows > INT32_MAX / 2) return DCTPLUS_ERR_UNSUPPORTED;
+        if (total_elems >= 0 && off + rows * g->plans[pi]->n > total_elems)
+            return DCTPLUS_ERR_INVALID_ARG;
+    }
+    return DCTPLUS_OK;
+}
+
+dctplus_status dctplus_execute_group(dctplus_group_t g, const float* x_dev, float* y_dev,
+                                     const int64_t* seg_host, int nseg, dctplus_stream_t stream) {
+    if (!g) return DCTPLUS_ERR_INVALID_ARG;
+    dctplus_status st = check_segments(g, seg_host, nseg, -1);
+    if (st != DCTPLUS_OK) return st;
+    if (nseg == 0) return DCTPLUS_OK;
+    if (!x_dev || !y_dev || x_dev == y_dev || !aligned16(x_dev) || !aligned16(y_dev))
+        return DCTPLUS_ERR_INVALID_ARG;
+    if ((st = check_device(g->device)) != DCTPLUS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = group_prepare(g, seg_host, nseg, s)) != DCTPLUS_OK) return st;
+    if (group_tc_available(g)) return launch_group_tc(g, x_dev, y_dev, s);
+    return launch_group_simt(g, x_dev, y_dev, s);
+}
+
+dctplus_status dctplus_execute_group_host(dctplus_group_t g, const float* x_host, float* y_host,
+                                          int64_t total_elems, const int64_t* seg_host, int nseg,
+                                          dctplus_stream_t stream) {
+    if (!g || total_elems < 0 || (total_elems > 0 && (!x_host || !y_host)))
+        return DCTPLUS_ERR_INVALID_ARG;
+    dctplus_status st = check_segments(g, seg_host, nseg, total_elems);
+    if (st != DCTPLUS_OK) return st;
+    if (total_elems == 0 || nseg == 0) return DCTPLUS_OK;
+    if ((st = check_device(g->device)) != DCTPLUS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t bytes = sizeof(float) * (size_t)total_elems;
+    size_t half = (bytes + 255) & ~size_t(255);
+    if (g->stage_bytes < 2 * half) {
+        if (g->d_stage) { cudaStreamSynchronize(s); cudaFree(g->d_stage); g->d_stage = nullptr; }
+        DCTPLUS_CUDA_TRY(cudaMalloc(&g->d_stage, 2 * half));
+        g->stage_bytes = 2 * half;
+    }
+    float* dx = static_cast<float*>(g->d_stage);
+    float* dy = reinterpret_cast<float*>(static_cast<char*>(g->d_stage) + half);
+    DCTPLUS_CUDA_TRY(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, s));
+    st = dctplus_execute_group(g, dx, dy, seg_host, nseg, stream);
+    if (st != DCTPLUS_OK) return st;
+    DCTPLUS_CUDA_TRY(cudaMemcpyAsync(y_host, dy, bytes, cudaMemcpyDeviceToHost, s));
+    DCTPLUS_CUDA_TRY(cudaStreamSynchronize(s));
+    return DCTPLUS_OK;
+}
+
+dctplus_status dctplus_sync_check(dctplus_stream_t stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DCTPLUS_CUDA_TRY(cudaStreamSynchronize(s));
+    int dev = 0;
+    DCTPLUS_CUDA_TRY(cudaGetDevice(&dev));
+    unsigned* w = device_error_word(dev);
+    if (!w) return DCTPLUS_ERR_CUDA;
+    unsigned h = 0;
+    DCTPLUS_CUDA_TRY(cudaMemcpy(&h, w, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (h) DCTPLUS_CUDA_TRY(cudaMemset(w, 0, sizeof(unsigned)));
+    if (h & kErrTimeout) return DCTPLUS_ERR_TIMEOUT;
+    if (h) return DCTPLUS_ERR_DEVICE_CHECK;
+    return DCTPLUS_OK;
+}
+
+}  // extern "C"

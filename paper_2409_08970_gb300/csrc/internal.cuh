@@ -1,0 +1,124 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "../../include/dctplus.h"
+
+namespace dctplus {
+
+constexpr int kMaxN = 16384;
+constexpr int kSmallMax = 64;      // n <= 64: fused small-n kernels
+constexpr int kTableMax = 4096;    // n <= 4096: a stored FP32 Cauchy table is allowed
+constexpr int kF64Max = 1024;      // FP64 execute path
+
+// Device error word bits (dctplus_sync_check).
+constexpr unsigned kErrIndex = 1u;    // an index guard fired
+constexpr unsigned kErrTimeout = 2u;  // a bounded wait gave up
+
+extern std::atomic<int64_t> g_launches;
+
+// Every kernel launch goes through this so dctplus_launch_count is exact.
+inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+unsigned* device_error_word(int device);  // lazily allocated per device
+
+// Device tables of the hierarchical Cauchy evaluation (see cauchy_hier.cu).
+struct HierTables;
+
+// Tables consumed by the tensor-core small-n kernel (see small_tc.cu).
+struct SmallTcTables {
+    // 64x64 block-diagonal operands, each as an FP32 image already in the
+    // K-major 128-byte-swizzled shared-memory layout the MMA reads:
+    // [0] DCT hi, [1] DCT lo, [2] W hi, [3] W lo; 16 KB each.
+    float* images = nullptr;
+};
+
+}  // namespace dctplus
+
+struct dctplus_plan_s {
+    int n = 0;
+    double rho = 0.0;
+    int device = 0;
+    int cauchy_mode = DCTPLUS_CAUCHY_AUTO;
+    std::vector<double> v;
+
+    // host copies of the setup stage, per output row r (ascending eigenvalue)
+    std::vector<double> eig, z, row_tau, row_a;
+    std::vector<int> row_kind, row_pole;
+    int K = 0;  // number of secular roots (non-deflated poles)
+
+    // device tables
+    double* d_z = nullptr;         // n
+    double* d_sin = nullptr;       // 2n+1: sin(pi m / 2n)
+    double* d_row_tau = nullptr;   // n
+    double* d_row_a = nullptr;     // n
+    int* d_row_kind = nullptr;     // n
+    int* d_row_pole = nullptr;     // n
+    float* d_ct32 = nullptr;       // n x n, U^T row-major (n <= 64)
+    double* d_ct64 = nullptr;      // n x n, U^T row-major (F64 path, n <= 1024)
+    float* d_w32 = nullptr;        // n x n, W = X^T U row-major (n <= 4096)
+    double* d_w64 = nullptr;       // n x n (F64 path, n <= 1024)
+    float* d_twiddle = nullptr;    // FFT DCT tables (n >= 128)
+    // per-row generator data for on-chip Cauchy tiles (FP32): pole, tau, -a
+    int* d_gen_pole = nullptr;
+    float* d_gen_tau = nullptr;
+    float* d_gen_na = nullptr;
+    float* d_gen_z = nullptr;      // z_k in FP32 (0 where deflated)
+    float* d_gen_sin = nullptr;    // sin(pi m / 2n), FP32, m = 0..2n
+    dctplus::SmallTcTables tc;
+    dctplus::HierTables* hier = nullptr;
+
+    // staging for dctplus_execute_host
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+struct dctplus_group_s {
+    int device = 0;
+    std::vector<dctplus_plan_t> plans;
+    // device table of plan pointers for the persistent kernel
+    void* d_plan_tables = nullptr;
+    int64_t* d_seg = nullptr;
+    int seg_cap = 0;
+    std::vector<int64_t> seg_cache;
+    int* d_tiles = nullptr;  // per-tile work list (see small kernels)
+    int tile_cap = 0;
+    int ntiles = 0;
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+#define DCTPLUS_CUDA_TRY(expr)                                  \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return DCTPLUS_ERR_CUDA;         \
+    } while (0)
+
+namespace dctplus {
+
+// plan.cu
+dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o);
+void free_plan_tables(dctplus_plan_t p);
+
+// small_simt.cu
+dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
+                                     int64_t ldy, int64_t batch, cudaStream_t s);
+dctplus_status launch_small_simt_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
+                                     int64_t ldy, int64_t batch, cudaStream_t s);
+
+// large.cu
+dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
+                              int64_t lds, int64_t batch, cudaStream_t st);
+dctplus_status launch_cauchy_simt(dctplus_plan_t p, const float* s_in, int64_t lds, float* y,
+                                  int64_t ldy, int64_t batch, cudaStream_t st);
+dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
+                                int64_t ldy, int64_t batch, cudaStream_t st);
+dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
+                                int64_t ldy, int64_t batch, cudaStream_t st);
+
+}  // namespace dctplus

@@ -1,0 +1,300 @@
+// Large-n pieces (n a power of two, 128 <= n <= 16384), FP32 data.
+//
+// DCT-II (Algorithm 1 step 1) by Makhoul's reordering: v_k = x_2k,
+// v_{n-1-k} = x_{2k+1}; the length-n DFT of the real sequence v comes from one
+// complex FFT of length M = n/2 on w_m = v_2m + i v_2m+1 (radix-2 Stockham in
+// shared memory), and X_k = Re(exp(-i pi k / 2n) V_k), X_{n-k} = -Im(...).
+// The orthonormal scale c_k is folded into the last step.
+//
+// Cauchy product (Algorithm 1 steps 2-8 with a and z folded into
+// W_rk = -a_r z_k / (mu_r - lambda_k)): y = W s as a tiled CUDA-core GEMM. W
+// comes from the plan's FP32 table (n <= 4096) or is generated tile by tile
+// in shared memory from per-row (pole, tau, -a) and per-column z.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace dctplus {
+
+// ------------------------------------------------------------------ tables
+
+// twiddles: [0, M/2): exp(-2 pi i j / M); [M/2, M/2 + M + 1): exp(-2 pi i k / n), k = 0..M;
+// [3M/2 + 1, 5M/2 + 2): c_k exp(-i pi k / 2n), k = 0..M
+__global__ void k_fft_tables(int n, float2* tw) {
+    int M = n / 2;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < M / 2) {
+        double s, c;
+        sincospi(-2.0 * idx / M, &s, &c);
+        tw[idx] = make_float2((float)c, (float)s);
+    } else if (idx < M / 2 + M + 1) {
+        int k = idx - M / 2;
+        double s, c;
+        sincospi(-2.0 * k / n, &s, &c);
+        tw[idx] = make_float2((float)c, (float)s);
+    } else if (idx < M / 2 + 2 * (M + 1)) {
+        int k = idx - (M / 2 + M + 1);
+        double s, c;
+        sincospi(-(double)k / (2.0 * n), &s, &c);
+        double ck = (k == 0) ? sqrt(1.0 / n) : sqrt(2.0 / n);
+        tw[idx] = make_float2((float)(ck * c), (float)(ck * s));
+    }
+}
+
+dctplus_status setup_large(dctplus_plan_t p) {
+    int n = p->n;
+    if (n & (n - 1)) return DCTPLUS_OK;  // FFT path only for powers of two
+    int M = n / 2;
+    size_t cnt = M / 2 + 2 * (M + 1);
+    DCTPLUS_CUDA_TRY(cudaMalloc((void**)&p->d_twiddle, sizeof(float2) * cnt));
+    k_fft_tables<<<(int)((cnt + 255) / 256), 256>>>(n, reinterpret_cast<float2*>(p->d_twiddle));
+    count_launch();
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+// ------------------------------------------------------------------ DCT-II
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// One CTA per signal (grid-stride over the batch).
+__global__ void __launch_bounds__(512) k_dct_fft(int n, const float* __restrict__ x, int64_t ldx,
+                                                 float* __restrict__ s, int64_t lds, int64_t batch,
+                                                 const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = n / 2;
+    float2* a = reinterpret_cast<float2*>(smem_raw);
+    float2* b = a + M;
+    const float2* tw_fft = tw;
+    const float2* tw_split = tw + M / 2;
+    const float2* tw_post = tw + M / 2 + M + 1;
+    for (int64_t sig = blockIdx.x; sig < batch; sig += gridDim.x) {
+        const float* xs = x + sig * ldx;
+        __syncthreads();
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            int q0 = 2 * m, q1 = 2 * m + 1;
+            float v0 = q0 < M ? xs[2 * q0] : xs[2 * n - 2 * q0 - 1];
+            float v1 = q1 < M ? xs[2 * q1] : xs[2 * n - 2 * q1 - 1];
+            a[m] = make_float2(v0, v1);
+        }
+        __syncthreads();
+        float2* src = a;
+        float2* dst = b;
+        for (int Ns = 1; Ns < M; Ns <<= 1) {
+            int tstep = M / (2 * Ns);
+            for (int j = threadIdx.x; j < M / 2; j += blockDim.x) {
+                int k = j & (Ns - 1);
+                float2 v0 = src[j];
+                float2 v1 = cmul(src[j + M / 2], tw_fft[k * tstep]);
+                int o = ((j - k) << 1) + k;
+                dst[o] = make_float2(v0.x + v1.x, v0.y + v1.y);
+                dst[o + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+            }
+            __syncthreads();
+            float2* t = src; src = dst; dst = t;
+        }
+        float* ss = s + sig * lds;
+        for (int k = threadIdx.x; k <= M; k += blockDim.x) {
+            float2 wk = src[k == M ? 0 : k];
+            float2 wm = src[(M - k) == M ? 0 : (M - k)];
+            float2 wmc = make_float2(wm.x, -wm.y);
+            float2 fe = make_float2(0.5f * (wk.x + wmc.x), 0.5f * (wk.y + wmc.y));
+            float2 d = make_float2(wk.x - wmc.x, wk.y - wmc.y);
+            float2 fo = make_float2(0.5f * d.y, -0.5f * d.x);  // d / (2i)
+            float2 vk = make_float2(fe.x, fe.y);
+            float2 t = cmul(tw_split[k], fo);
+            vk.x += t.x; vk.y += t.y;
+            float2 bq = cmul(tw_post[k], vk);  // c_k exp(-i pi k/2n) V_k
+            if (k == 0) {
+                ss[0] = bq.x;
+            } else if (k == M) {
+                ss[M] = bq.x;
+            } else {
+                ss[k] = bq.x;
+                // X_{n-k} = -Im(exp(-i pi k/2n) V_k); c_{n-k} = c_k for k > 0
+                ss[n - k] = -bq.y;
+            }
+        }
+    }
+}
+
+dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
+                              int64_t lds, int64_t batch, cudaStream_t st) {
+    int n = p->n;
+    if (!p->d_twiddle) return DCTPLUS_ERR_UNSUPPORTED;
+    size_t smem = sizeof(float2) * n;  // two buffers of n/2
+    static bool attr[64] = {};
+    if (!attr[p->device & 63]) {
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr[p->device & 63] = true;
+    }
+    int threads = std::min(512, std::max(32, n / 4));
+    int64_t grid = std::min<int64_t>(batch, 152 * std::max(1, (int)(200 * 1024 / std::max<size_t>(smem, 1)) ));
+    grid = std::min<int64_t>(grid, 65535 * 16);
+    if (grid <= 0) return DCTPLUS_OK;
+    k_dct_fft<<<(unsigned)grid, threads, smem, st>>>(n, x, ldx, s_out, lds, batch,
+                                                     reinterpret_cast<const float2*>(p->d_twiddle));
+    count_launch();
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+// ------------------------------------------------------- Cauchy (CUDA cores)
+
+// W_rk generated in FP32 from the per-row generator: pole >= 0 is the origin
+// pole of a root row (mu_r = lambda_pole + tau_r), pole < 0 marks the deflated
+// row e_{-1-pole}.
+__device__ __forceinline__ float gen_w(int k, int pole, float tau, float na, const float* gz,
+                                       const float* gsin, int n) {
+    if (pole < 0) return (k == -1 - pole) ? 1.0f : 0.0f;
+    float zk = gz[k];
+    if (zk == 0.0f) return 0.0f;
+    int m = k + pole;
+    m = min(m, 2 * n - m);
+    int q = k - pole;
+    float s2 = q >= 0 ? gsin[q] : -gsin[-q];
+    float d = 4.0f * gsin[m] * s2;  // lambda_k - lambda_pole
+    return na * zk / (tau - d);      // -a_r z_k / (mu_r - lambda_k)
+}
+
+constexpr int kGB = 64;  // signals per tile
+constexpr int kGR = 64;  // output rows per tile
+constexpr int kGK = 16;
+
+// y[b][r] = sum_k s[b][k] W[r][k]; 256 threads, 4x4 outputs per thread.
+__global__ void __launch_bounds__(256) k_cauchy_simt(int n, const float* __restrict__ s,
+                                                     int64_t lds, float* __restrict__ y,
+                                                     int64_t ldy, int64_t batch,
+                                                     const float* __restrict__ wtab,
+                                                     const int* __restrict__ gpole,
+                                                     const float* __restrict__ gtau,
+                                                     const float* __restrict__ gna,
+                                                     const float* __restrict__ gz,
+                                                     const float* __restrict__ gsin) {
+    __shared__ float As[kGK][kGB + 4];
+    __shared__ float Bs[kGK][kGR + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t b0 = (int64_t)blockIdx.y * kGB;
+    const int r0 = blockIdx.x * kGR;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < n; k0 += kGK) {
+        for (int e = tid; e < kGB * kGK; e += 256) {
+            int bb = e / kGK, kk = e % kGK;
+            int64_t b = b0 + bb;
+            As[kk][bb] = (b < batch) ? s[b * lds + k0 + kk] : 0.0f;
+        }
+        for (int e = tid; e < kGR * kGK; e += 256) {
+            int rr = e / kGK, kk = e % kGK;
+            int r = r0 + rr, k = k0 + kk;
+            float wv = 0.0f;
+            if (r < n) {
+                if (wtab) wv = wtab[(int64_t)r * n + k];
+                else wv = gen_w(k, gpole[r], gtau[r], gna[r], gz, gsin, n);
+            }
+            Bs[kk][rr] = wv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t b = b0 + ty * 4 + i;
+        if (b >= batch) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int r = r0 + tx * 4 + j;
+            if (r < n) y[b * ldy + r] = acc[i][j];
+        }
+    }
+}
+
+dctplus_status launch_cauchy_simt(dctplus_plan_t p, const float* s_in, int64_t lds, float* y,
+                                  int64_t ldy, int64_t batch, cudaStream_t st) {
+    int n = p->n;
+    if (n % kGK) return DCTPLUS_ERR_UNSUPPORTED;
+    int64_t gy = (batch + kGB - 1) / kGB;
+    if (gy > 65535) return DCTPLUS_ERR_UNSUPPORTED;
+    dim3 grid((n + kGR - 1) / kGR, (unsigned)gy);
+    k_cauchy_simt<<<grid, 256, 0, st>>>(n, s_in, lds, y, ldy, batch, p->d_w32, p->d_gen_pole,
+                                        p->d_gen_tau, p->d_gen_na, p->d_gen_z, p->d_gen_sin);
+    count_launch();
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+// ------------------------------------------------------------ FP64 (n <= 1024)
+
+// One CTA per signal: s = U^T x, then y = W s, both from the plan's FP64
+// tables; one warp per output coefficient with lanes over the inner index.
+__global__ void __launch_bounds__(256) k_dense_f64(int n, const double* __restrict__ x,
+                                                   int64_t ldx, double* __restrict__ y,
+                                                   int64_t ldy, int64_t batch,
+                                                   const double* __restrict__ ct,
+                                                   const double* __restrict__ w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* xs = reinterpret_cast<double*>(smem_raw);
+    double* ss = xs + n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = x[b * ldx + j];
+        __syncthreads();
+        for (int k = warp; k < n; k += nw) {
+            double acc = 0.0;
+            for (int j = lane; j < n; j += 32) acc = fma(ct[(int64_t)k * n + j], xs[j], acc);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) ss[k] = acc;
+        }
+        __syncthreads();
+        for (int r = warp; r < n; r += nw) {
+            double acc = 0.0;
+            for (int k = lane; k < n; k += 32) acc = fma(w[(int64_t)r * n + k], ss[k], acc);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) y[b * ldy + r] = acc;
+        }
+    }
+}
+
+dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
+                                int64_t ldy, int64_t batch, cudaStream_t st) {
+    if (!p->d_ct64 || !p->d_w64) return DCTPLUS_ERR_UNSUPPORTED;
+    int64_t grid = std::min<int64_t>(batch, 152 * 8);
+    k_dense_f64<<<(unsigned)grid, 256, sizeof(double) * 2 * p->n, st>>>(p->n, x, ldx, y, ldy, batch,
+                                                                        p->d_ct64, p->d_w64);
+    count_launch();
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+// Per-stream scratch for the DCT output s (batch x n floats).
+void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes);
+
+dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
+                                int64_t ldy, int64_t batch, cudaStream_t st) {
+    int n = p->n;
+    if (n & (n - 1)) return DCTPLUS_ERR_UNSUPPORTED;
+    float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * (size_t)batch * n));
+    if (!ws) return DCTPLUS_ERR_CUDA;
+    dctplus_status r = launch_dct_fft(p, x, ldx, ws, n, batch, st);
+    if (r != DCTPLUS_OK) return r;
+    return launch_cauchy_simt(p, ws, n, y, ldy, batch, st);
+}
+
+}  // namespace dctplus
