@@ -119,8 +119,10 @@ int dctplus_plan_cauchy_mode(dctplus_plan_t plan);
  * y_b = X^T x_b for b = 0..batch-1.
  *   dtype : DCTPLUS_F32 (split-TF32 tensor-core contractions, FP32 in/out) or
  *           DCTPLUS_F64 (FP64 CUDA-core path, n <= 1024).
- *   x_dev, y_dev: device pointers, 16-byte aligned, rows of n elements with
- *           leading dimensions ldx, ldy >= n (multiples of 4 for F32, 2 for F64).
+ *   x_dev, y_dev: device pointers aligned to the element size, rows of n
+ *           elements with leading dimensions ldx, ldy >= n. The tensor-core
+ *           kernels run when both bases are 16-byte aligned and ldx, ldy are
+ *           multiples of 4; other layouts take the CUDA-core kernels.
  *           x and y must not overlap.
  *   batch : number of signals, >= 0 (0 is a no-op).
  * Asynchronous on `stream`. Errors: INVALID_ARG, UNSUPPORTED, CUDA. */

@@ -186,9 +186,9 @@ static dctplus_status check_exec_args(dctplus_plan_t p, dctplus_dtype dtype, con
     if (batch == 0) return DCTPLUS_OK;
     if (!x || !y || x == y) return DCTPLUS_ERR_INVALID_ARG;
     if (ldx < p->n || ldy < p->n) return DCTPLUS_ERR_INVALID_ARG;
-    int q = dtype == DCTPLUS_F32 ? 4 : 2;
-    if (ldx % q || ldy % q || !aligned16(x) || !aligned16(y)) return DCTPLUS_ERR_INVALID_ARG;
     size_t es = dtype == DCTPLUS_F32 ? 4 : 8;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & (es - 1))
+        return DCTPLUS_ERR_INVALID_ARG;
     // reject overlapping x / y ranges
     uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
     uintptr_t xe = xa + es * (size_t)((batch - 1) * ldx + p->n);

@@ -199,6 +199,9 @@ __global__ void __launch_bounds__(256) k_cauchy_simt(int n, const float* __restr
             Bs[kk][rr] = wv;
         }
         __syncthreads();
+        // two-level accumulation: a fresh partial per K tile keeps the FP32
+        // rounding error of a length-n dot product near sqrt(n/16) eps
+        float part[4][4] = {};
 #pragma unroll
         for (int kk = 0; kk < kGK; ++kk) {
             float av[4], bv[4];
@@ -209,8 +212,12 @@ __global__ void __launch_bounds__(256) k_cauchy_simt(int n, const float* __restr
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
         __syncthreads();
     }
 #pragma unroll

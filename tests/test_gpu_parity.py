@@ -170,10 +170,16 @@ def test_edge_cases(pkg):
     y = plan.forward(xt).double().cpu().numpy()
     ref = cauchy.transform(cauchy.make_plan(n, self_loop_v(n, 0), 1.0), xb[:, :n])
     assert relerr(y, ref).max() < F32_TOL
-    # misaligned pointer is rejected on the host
-    big = torch.zeros((4, n + 1), device="cuda")
-    with pytest.raises(pkg.DctPlusError):
-        plan.forward(big[:, 1:])
+    # a view offset by one element (not 16-byte aligned, ld = n + 1) still transforms correctly
+    xo = normal_signals(9, n + 1, seed=2)
+    big = torch.tensor(xo, dtype=torch.float32, device="cuda")
+    y = plan.forward(big[:, 1:]).double().cpu().numpy()
+    assert relerr(y, cauchy.transform(cauchy.make_plan(n, self_loop_v(n, 0), 1.0), xo[:, 1:])).max() < F32_TOL
+    # a pointer not aligned to the element size is rejected on the host
+    with pytest.raises(pkg.DctPlusError) as e:
+        pkg.dctplus_execute(plan.handle, pkg.F32, big.data_ptr() + 2, n + 1, big.data_ptr() + 4096,
+                            n + 1, 1, 0)
+    assert e.value.status == 1
     assert pkg.dctplus_sync_check(0) == 0
     plan.close()
 
