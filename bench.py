@@ -1,0 +1,402 @@
+"""Benchmark of the batched Fast DCT+ forward transform on GB300.
+
+Headline workload (one "step" = one forward pass over the whole batch):
+mixed-size rows, 2^20 rows with n drawn uniformly from {4, 8, 16, 32, 64},
+integer Laplace(12) residuals clipped to [-255, 255] in FP32, four rank-one
+updates per size (self-loop at vertex 0 with rho in {0.5, 1, 2}, central-edge
+weight change rho = -0.5), all 20 (size, update) segments in one persistent
+launch replayed from a CUDA graph. A second line item times n = 1024 signals
+(batch 4096, dense random unit v, rho in {-0.3, 2.0}).
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "transform GSamples/s + %roofline at n=64/1024 vs dense-GFT GEMM, same GPU, FP32 err"
+WORKLOAD = ("mixed-size forward: 2^20 rows, n uniform in {4,8,16,32,64}, rint(Laplace(0,12)) "
+            "clipped to [-255,255] FP32, 4 rank-one updates per size (self-loop at vertex 0, "
+            "rho in {0.5,1,2}; edge (n/2-1,n/2), rho=-0.5), one persistent launch per step from a "
+            "CUDA graph")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_mixed(pkg):
+    from synthetic import mixed_size_workload
+    wl = mixed_size_workload()
+    plans, index = [], {}
+    for n, ups in wl.updates.items():
+        for u, (v, rho) in enumerate(ups):
+            index[(n, u)] = len(plans)
+            plans.append(pkg.Plan(n, v, rho))
+    seg = np.array([[index[(s.n, s.update)], s.offset, s.rows] for s in wl.segments], dtype=np.int64)
+    return wl, plans, seg
+
+
+def time_graph(fn, stream, steps, warmup, flush):
+    """Capture fn() in a CUDA graph; time `steps` replays with events, flushing L2 between."""
+    import torch
+    fn()  # first call uploads tables / allocates scratch outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        flush()
+        g.replay()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for e0, e1 in evs:
+            flush()
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in evs], g
+
+
+def run_ours(args):
+    import torch
+    import paper_2409_08970_gb300 as pkg
+    from paper_2409_08970_gb300 import build as _build
+    rank, world, local = dist_setup()
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    hbm_peak, bf16_peak, peak_src = load_peaks()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    wl, plans, seg = make_mixed(pkg)
+    group = pkg.Group(plans)
+    x = torch.tensor(wl.x, device=dev)
+    y = torch.empty_like(x)
+    samples = wl.total_samples
+    sh = stream.cuda_stream
+
+    def step():
+        pkg.dctplus_execute_group(group.handle, x.data_ptr(), y.data_ptr(), seg, sh)
+
+    lc0 = pkg.dctplus_launch_count()
+    step()
+    torch.cuda.synchronize()
+    launches_per_step = pkg.dctplus_launch_count() - lc0
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    times, graph = time_graph(step, stream, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    t_ms = float(np.mean(times))
+    t_ms_max = max_over_ranks(t_ms, world)
+    value = world * samples / (t_ms_max * 1e-3) / 1e9
+    algo_bytes = 8.0 * samples  # read x + write y, FP32
+    achieved = algo_bytes / (t_ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer C entry point (pinned host memory)
+    xh = torch.empty(x.numel(), dtype=torch.float32, pin_memory=True)
+    xh.copy_(torch.from_numpy(wl.x))
+    yh = torch.empty_like(xh)
+    xh_np, yh_np = xh.numpy(), yh.numpy()
+
+    def e2e_step():
+        pkg.dctplus_execute_group_host(group.handle, xh_np.ctypes.data, yh_np.ctypes.data,
+                                       xh_np.size, seg, sh)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    t_e2e = max_over_ranks(t_e2e, world)
+    e2e = {"value": world * samples / t_e2e / 1e9, "unit": "GSamples/s",
+           "h2d_bytes_per_step": int(4 * samples), "d2h_bytes_per_step": int(4 * samples),
+           "ms_per_step": t_e2e * 1e3}
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["n1024"] = bench_n1024(pkg, torch, dev, stream, args, flush, hbm_peak)
+        extra["dense_gft_cublas_fp32"] = bench_dense_gft(pkg, torch, dev, stream, args, flush, wl,
+                                                         plans, seg)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, y.cpu().numpy())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GSamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": int(wl.total_rows), "samples": int(samples),
+                       "segments": int(seg.shape[0]), "l2": "flushed (256 MiB write) between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_small_simt<float>",
+                         "algorithmic_bytes_per_launch": algo_bytes},
+            "e2e": e2e,
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clk,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu["baseline"]
+            line["fp32_err_vs_fp64_oracle"] = cpu["err"]
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_n1024(pkg, torch, dev, stream, args, flush, hbm_peak):
+    from synthetic import normal_signals, random_unit_v
+    n, batch = 1024, 4096
+    v = random_unit_v(n)
+    plans = [pkg.Plan(n, v, rho) for rho in (-0.3, 2.0)]
+    x = torch.tensor(normal_signals(batch, n, seed=0), dtype=torch.float32, device=dev)
+    ys = [torch.empty_like(x) for _ in plans]
+    sh = stream.cuda_stream
+
+    def step():
+        for p, y in zip(plans, ys):
+            pkg.dctplus_execute(p.handle, pkg.F32, x.data_ptr(), n, y.data_ptr(), n, batch, sh)
+
+    times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
+    t_ms = float(np.mean(times))
+    samples = 2 * batch * n
+    return {"workload": "n=1024, batch 4096, x~N(0,1), dense unit v (seed 1), rho in {-0.3, 2.0}",
+            "value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t_ms,
+            "cauchy_mode": plans[0].cauchy_mode,
+            "hbm_frac_of_measured": 8.0 * samples / (t_ms * 1e-3) / 1e9 / hbm_peak}
+
+
+def bench_dense_gft(pkg, torch, dev, stream, args, flush, wl, plans, seg):
+    """Non-product reference point: cuBLAS FP32 GEMM against the dense X^T per segment.
+
+    X^T comes from this library's FP64 transform of the identity (rows of I).
+    """
+    torch.backends.cuda.matmul.allow_tf32 = False
+    mats = []
+    for p in plans:
+        eye = torch.eye(p.n, dtype=torch.float64, device=dev)
+        mats.append(p.forward(eye).t().contiguous().float())  # X^T
+    x = torch.tensor(wl.x, device=dev)
+    y = torch.empty_like(x)
+    views = []
+    for pi, off, rows in seg:
+        n = plans[pi].n
+        views.append((x[off:off + rows * n].view(rows, n), y[off:off + rows * n].view(rows, n),
+                      mats[pi].t()))
+
+    def step():
+        for xs, ys, m in views:
+            torch.matmul(xs, m, out=ys)
+
+    with torch.cuda.stream(stream):
+        times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
+    t_ms = float(np.mean(times))
+    return {"value": wl.total_samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s",
+            "ms_per_step": t_ms, "kind": "cuBLAS SGEMM per segment (FP32, no TF32), same workload"}
+
+
+def cpu_baseline(wl, y_gpu):
+    """The FP64 oracle (Cauchy formula, O2) as it stands, on the host cores."""
+    from oracle import cauchy
+    plans = {(n, u): cauchy.make_plan(n, v, rho) for n, ups in wl.updates.items()
+             for u, (v, rho) in enumerate(ups)}
+    t0 = time.perf_counter()
+    outs = []
+    for s in wl.segments:
+        xs = wl.x[s.offset:s.offset + s.rows * s.n].astype(np.float64).reshape(s.rows, s.n)
+        outs.append(cauchy.transform(plans[(s.n, s.update)], xs))
+    dt = time.perf_counter() - t0
+    errs, maxabs = [], 0.0
+    for s, ref in zip(wl.segments, outs):
+        got = y_gpu[s.offset:s.offset + s.rows * s.n].astype(np.float64).reshape(s.rows, s.n)
+        nr = np.linalg.norm(ref, axis=1)
+        ok = nr > 0
+        errs.append(np.linalg.norm(got - ref, axis=1)[ok] / nr[ok])
+        maxabs = max(maxabs, float(np.abs(got - ref).max()))
+    e = np.concatenate(errs)
+    return {"baseline": {"value": wl.total_samples / dt / 1e9, "unit": "GSamples/s",
+                         "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                         "sample": "the whole workload (all 2^20 rows), one pass, plans excluded; "
+                                   "FP64 numpy/BLAS on all host cores"},
+            "err": {"normwise_rel_max": float(e.max()), "normwise_rel_mean": float(e.mean()),
+                    "max_abs": maxabs, "snr_db_mean": float(np.mean(-20 * np.log10(np.maximum(e, 1e-300))))}}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host, same workload, bounded steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import cauchy
+    from synthetic import mixed_size_workload
+    wl = mixed_size_workload()
+    plans = {(n, u): cauchy.make_plan(n, v, rho) for n, ups in wl.updates.items()
+             for u, (v, rho) in enumerate(ups)}
+
+    def step():
+        for s in wl.segments:
+            xs = wl.x[s.offset:s.offset + s.rows * s.n].astype(np.float64).reshape(s.rows, s.n)
+            cauchy.transform(plans[(s.n, s.update)], xs)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = wl.total_samples / dt / 1e9
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GSamples/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": int(wl.total_rows), "samples": int(wl.total_samples)},
+            "cpu_baseline": {"value": value, "unit": "GSamples/s", "cores": cores, "kind": "oracle",
+                             "sample": "the whole workload per step (FP64 Cauchy-formula oracle, "
+                                       "numpy/BLAS on the host cores, plans excluded)"},
+            "e2e": {"value": value, "unit": "GSamples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true", help="skip the n=1024 and comparator items")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -15,8 +15,6 @@ dctplus_status group_prepare(dctplus_group_t g, const int64_t* seg_host, int nse
                              cudaStream_t s);                                // small_simt.cu
 dctplus_status group_upload_plans(dctplus_group_t g);                        // small_simt.cu
 dctplus_status launch_group_simt(dctplus_group_t g, const float* x, float* y, cudaStream_t s);
-dctplus_status launch_group_tc(dctplus_group_t g, const float* x, float* y, cudaStream_t s);
-bool group_tc_available(dctplus_group_t g);
 
 static std::mutex g_err_mu;
 static unsigned* g_err_words[64] = {};
@@ -300,13 +298,34 @@ dctplus_status dctplus_execute_group(dctplus_group_t g, const float* x_dev, floa
     dctplus_status st = check_segments(g, seg_host, nseg, -1);
     if (st != DCTPLUS_OK) return st;
     if (nseg == 0) return DCTPLUS_OK;
-    if (!x_dev || !y_dev || x_dev == y_dev || !aligned16(x_dev) || !aligned16(y_dev))
-        return DCTPLUS_ERR_INVALID_ARG;
+    if (!x_dev || !y_dev || x_dev == y_dev) return DCTPLUS_ERR_INVALID_ARG;
     if ((st = check_device(g->device)) != DCTPLUS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if ((st = group_prepare(g, seg_host, nseg, s)) != DCTPLUS_OK) return st;
-    if (group_tc_available(g)) return launch_group_tc(g, x_dev, y_dev, s);
-    return launch_group_simt(g, x_dev, y_dev, s);
+    // full packed 64-sample rows of tensor-core-capable plans go to the
+    // tensor-core kernel; their leftover signals and all other plans to the
+    // CUDA-core kernel
+    const bool tc_ok = aligned16(x_dev) && aligned16(y_dev);
+    std::vector<TcSegHost> tc;
+    std::vector<int64_t> simt;
+    for (int i = 0; i < nseg; ++i) {
+        int64_t pi = seg_host[3 * i], off = seg_host[3 * i + 1], rows = seg_host[3 * i + 2];
+        dctplus_plan_t p = g->plans[pi];
+        if (rows == 0) continue;
+        int64_t rows64 = (tc_ok && small_tc_capable(p)) ? rows * p->n / 64 : 0;
+        int64_t body = rows64 * 64 / p->n;
+        if (rows64 > 0) tc.push_back({p, x_dev + off, y_dev + off, rows64});
+        if (rows > body) {
+            simt.push_back(pi);
+            simt.push_back(off + body * p->n);
+            simt.push_back(rows - body);
+        }
+    }
+    if (!tc.empty() && (st = launch_tc_segments(tc, s, g->device)) != DCTPLUS_OK) return st;
+    if (!simt.empty()) {
+        if ((st = group_prepare(g, simt.data(), (int)simt.size() / 3, s)) != DCTPLUS_OK) return st;
+        return launch_group_simt(g, x_dev, y_dev, s);
+    }
+    return DCTPLUS_OK;
 }
 
 dctplus_status dctplus_execute_group_host(dctplus_group_t g, const float* x_host, float* y_host,

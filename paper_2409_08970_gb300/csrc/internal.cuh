@@ -101,6 +101,18 @@ struct dctplus_group_s {
 
 namespace dctplus {
 
+// One segment of packed 64-sample rows for the tensor-core kernel.
+struct TcSegHost {
+    dctplus_plan_t plan;
+    const float* x;
+    float* y;
+    int64_t rows64;
+};
+
+// small_tc.cu
+bool small_tc_capable(dctplus_plan_t p);
+dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream_t s, int dev);
+
 // plan.cu
 dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o);
 void free_plan_tables(dctplus_plan_t p);

@@ -245,3 +245,38 @@ def test_mixed_size_full_workload_sampled(pkg):
     group.close()
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64])
+def test_tensor_core_path_tiles_and_tails(pkg, n):
+    """Full packed rows go to the tcgen05 kernel, leftovers to the CUDA-core kernel."""
+    per = 64 // n  # signals per packed row
+    batches = [max(1, per - 1), 128 * per, 128 * per + max(1, per - 1), 129 * per,
+               (3 * 152 + 7) * 128 * per + max(1, per // 2)]
+    v, rho = random_unit_v(n, seed=7), 1.3
+    ref_plan = cauchy.make_plan(n, v, rho)
+    plan = pkg.Plan(n, v, rho)
+    simt = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_SIMT)
+    for batch in batches:
+        x = normal_signals(batch, n, seed=batch % 1000)
+        ref = cauchy.transform(ref_plan, x)
+        y = run32(plan, x)
+        assert relerr(y, ref).max() < F32_TOL, (n, batch, relerr(y, ref).max())
+        ys = run32(simt, x)
+        assert relerr(y, ys).max() < 2 * F32_TOL
+    assert pkg.dctplus_sync_check(0) == 0
+    plan.close()
+    simt.close()
+
+
+def test_tensor_core_path_integer_residuals(pkg):
+    """Laplace integer residuals (exact in TF32) through the tensor-core path, all sizes."""
+    for n in (4, 8, 16, 32, 64):
+        x = laplace_residuals(5000 * n, seed=n).astype(np.float64).reshape(5000, n)
+        for v, rho in [(self_loop_v(n, 0), 2.0), (edge_update_v(n, n // 2 - 1, n // 2), -0.5)]:
+            ref = cauchy.transform(cauchy.make_plan(n, v, rho), x)
+            plan = pkg.Plan(n, v, rho)
+            y = run32(plan, x)
+            nz = np.linalg.norm(ref, axis=1) > 0
+            assert relerr(y[nz], ref[nz]).max() < F32_TOL
+            plan.close()
