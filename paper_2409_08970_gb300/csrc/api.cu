@@ -301,9 +301,8 @@ dctplus_status dctplus_execute_group(dctplus_group_t g, const float* x_dev, floa
     if (!x_dev || !y_dev || x_dev == y_dev) return DCTPLUS_ERR_INVALID_ARG;
     if ((st = check_device(g->device)) != DCTPLUS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // full packed 64-sample rows of tensor-core-capable plans go to the
-    // tensor-core kernel; their leftover signals and all other plans to the
-    // CUDA-core kernel
+    // segments of tensor-core-capable plans go to the tensor-core kernel (one
+    // launch for all of them), the others to the CUDA-core kernel
     const bool tc_ok = aligned16(x_dev) && aligned16(y_dev);
     std::vector<TcSegHost> tc;
     std::vector<int64_t> simt;
@@ -311,13 +310,12 @@ dctplus_status dctplus_execute_group(dctplus_group_t g, const float* x_dev, floa
         int64_t pi = seg_host[3 * i], off = seg_host[3 * i + 1], rows = seg_host[3 * i + 2];
         dctplus_plan_t p = g->plans[pi];
         if (rows == 0) continue;
-        int64_t rows64 = (tc_ok && small_tc_capable(p)) ? rows * p->n / 64 : 0;
-        int64_t body = rows64 * 64 / p->n;
-        if (rows64 > 0) tc.push_back({p, x_dev + off, y_dev + off, rows64});
-        if (rows > body) {
+        if (tc_ok && small_tc_capable(p)) {
+            tc.push_back({p, x_dev + off, y_dev + off, rows});
+        } else {
             simt.push_back(pi);
-            simt.push_back(off + body * p->n);
-            simt.push_back(rows - body);
+            simt.push_back(off);
+            simt.push_back(rows);
         }
     }
     if (!tc.empty() && (st = launch_tc_segments(tc, s, g->device)) != DCTPLUS_OK) return st;

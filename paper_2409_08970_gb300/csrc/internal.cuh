@@ -101,12 +101,12 @@ struct dctplus_group_s {
 
 namespace dctplus {
 
-// One segment of packed 64-sample rows for the tensor-core kernel.
+// One segment of contiguous signals for the tensor-core kernel.
 struct TcSegHost {
     dctplus_plan_t plan;
     const float* x;
     float* y;
-    int64_t rows64;
+    int64_t rows;  // signals
 };
 
 // small_tc.cu

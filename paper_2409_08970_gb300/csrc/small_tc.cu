@@ -7,15 +7,26 @@
 // steps 2-8, with a and z folded into W = X^T U, Theorem 3.1) one product with
 // I_{64/n} (x) W. Per tile of 128 packed rows:
 //   S = X B1^T,  Y = S B2^T      (M = 128, N = 64, K = 64)
-// on the tensor cores in kind::tf32 with split operands: every FP32 operand
-// is a sum hi + lo of two TF32 numbers and each product takes the three terms
-// hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory (TMEM).
+// on the tensor cores in kind::tf32 with split operands: an FP32 operand is
+// hi + lo with hi, lo TF32, and a product takes hi*hi + hi*lo + lo*hi,
+// accumulated in FP32 in tensor memory (TMEM). For x and S the hi part is the
+// FP32 value itself, which the MMA reads truncated to TF32 (S straight from
+// its TMEM accumulator), and lo = rn_tf32(v - trunc_tf32(v)); for the plan's
+// matrices hi and lo are both rounded. The MMA accumulates like
+// round-toward-zero, so the two small correction products are issued first
+// and the hi*hi terms last: the large partial sums see 8 roundings, not 24.
 //
-// Roles (192 threads, one persistent CTA per SM):
-//   warp 0      TMA producer: x tiles into a 2-stage ring (128-byte swizzle)
-//   warp 1      TMEM owner and MMA issuer (one thread)
-//   warps 2..5  epilogue: x_lo = x - tf32(x); S from TMEM split into hi/lo
-//               tiles; Y from TMEM staged in shared memory and stored by TMA.
+// Pipeline: the DCT GEMM of tile t+1 is issued before the Cauchy GEMM of tile
+// t, so it runs while the epilogue forms tile t's S_lo.
+// Roles (480 threads, one persistent CTA per SM):
+//   warp 0       TMA producer: x tiles into a 3-stage ring (128-byte swizzle)
+//   warp 1       TMEM owner and MMA issuer (one thread)
+//   warps 2..9   x_lo into shared memory; S_lo from the S accumulator into
+//                TMEM; two warps per TMEM lane quarter, 32 columns each
+//   warps 10..13 Y (TMEM) staged in shared memory and stored by TMA
+//   warp 14      the < 64/n signals of each segment that do not fill a packed
+//                row, on CUDA cores from the plan's FP32 tables
+// TMEM columns: D1[3] 0..191, D2[2] 192..319, S_lo[2] 320..447.
 // Every mbarrier wait is bounded; a wait that runs out sets the device error
 // word and the CTA winds down (no trap, TMEM released).
 #include <cudaTypedefs.h>
@@ -31,22 +42,32 @@ namespace dctplus {
 
 constexpr int kTcMaxSeg = 40;
 constexpr int kTcRows = 128;
+constexpr int kStages = 3;
+constexpr int kTcThreads = 480;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 // shared-memory map (offsets from a 1024-byte aligned base)
 constexpr uint32_t kImgBytes = 16384;               // one 64x64 TF32 operand image
-constexpr uint32_t kOffB = 0;                       // B1 hi, B1 lo, B2 hi, B2 lo
-constexpr uint32_t kOffX = 4 * kImgBytes;           // 2 stages x 32 KB
 constexpr uint32_t kTileBytes = kTcRows * 64 * 4;   // 32 KB
-constexpr uint32_t kOffXlo = kOffX + 2 * kTileBytes;
-constexpr uint32_t kOffShi = kOffXlo + kTileBytes;
-constexpr uint32_t kOffSlo = kOffShi + kTileBytes;
-constexpr uint32_t kOffBar = kOffSlo + kTileBytes;
+constexpr uint32_t kOffB = 0;                       // B1 hi, B1 lo, B2 hi, B2 lo
+constexpr uint32_t kOffX = 4 * kImgBytes;           // kStages x 32 KB
+constexpr uint32_t kOffXlo = kOffX + kStages * kTileBytes;
+constexpr uint32_t kOffY = kOffXlo + kTileBytes;
+constexpr uint32_t kOffBar = kOffY + kTileBytes;
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;  // + barriers + alignment slack
 
+// TMEM column map
+constexpr uint32_t kColD1 = 0, kColD2 = 192, kColSlo = 320;
+
 struct TcSeg {
-    int tile_start;  // first tile index of the segment in this launch
-    int rows64;      // packed rows in the segment
+    int tile_start;     // first tile index of the segment in this launch
+    int rows64;         // packed rows in the segment
+    int n;
+    int tail;           // signals after the last full packed row
+    const float* xt;    // first tail signal
+    float* yt;
+    const float* ct;    // n x n FP32 U^T
+    const float* w;     // n x n FP32 W
 };
 
 struct TcParams {
@@ -66,47 +87,36 @@ __device__ __forceinline__ int find_seg(const TcParams& P, int tile) {
     return s;
 }
 
-// thread (row r) writes 64 FP32 values in the 128-byte-swizzled K-major layout
-__device__ __forceinline__ void store_row_sw128(unsigned char* base, int r, const float* v) {
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-        int kb = c >> 3, cc = c & 7;
-        float4 q = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-        *reinterpret_cast<float4*>(base + kb * kTileBytes / 2 + r * 128 + ((cc ^ (r & 7)) << 4)) = q;
-    }
+// byte offset of the 16-byte chunk c (0..15) of row r in a 128-row tile in the
+// 128-byte-swizzled K-major layout (K-block c / 8)
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
+    return (uint32_t)((c >> 3) * (kTileBytes / 2) + r * 128 + (((c & 7) ^ (r & 7)) << 4));
 }
 
-__device__ __forceinline__ void load_tmem_row64(uint32_t taddr, float* v) {
-    uint32_t r[16];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        ptx::tmem_ld16(taddr + 16 * j, r);
-        ptx::tmem_wait_ld();
-#pragma unroll
-        for (int e = 0; e < 16; ++e) v[16 * j + e] = __uint_as_float(r[e]);
-    }
+// the MMA reads v truncated to TF32; this is the rest, rounded to TF32
+__device__ __forceinline__ uint32_t lo_tf32(float v) {
+    return ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu));
 }
 
-__global__ void __launch_bounds__(192, 1) k_small_tc(const __grid_constant__ TcParams P) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constant__ TcParams P) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* Bimg = sm + kOffB;
     unsigned char* xbuf = sm + kOffX;
     unsigned char* xlo = sm + kOffXlo;
-    unsigned char* Shi = sm + kOffShi;
-    unsigned char* Slo = sm + kOffSlo;
+    unsigned char* ybuf = sm + kOffY;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
-    uint64_t* x_full = bars + 0;      // [2]
-    uint64_t* x_empty = bars + 2;     // [2]
-    uint64_t* d1_full = bars + 4;     // [2]
-    uint64_t* d2_full = bars + 6;     // [2]
-    uint64_t* tmem_empty = bars + 8;  // [2]
-    uint64_t* xlo_full = bars + 10;
-    uint64_t* s_full = bars + 11;
-    uint64_t* b_full = bars + 12;
-    uint64_t* drain = bars + 13;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+    uint64_t* x_full = bars + 0;    // [3]
+    uint64_t* x_empty = bars + 3;   // [3]
+    uint64_t* d1_full = bars + 6;   // [3]
+    uint64_t* s_full = bars + 9;    // [2]
+    uint64_t* d2_full = bars + 11;  // [2]
+    uint64_t* d2_empty = bars + 13; // [2]
+    uint64_t* xlo_full = bars + 15;
+    uint64_t* b_full = bars + 16;
+    uint64_t* drain = bars + 17;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 20);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -117,21 +127,23 @@ __global__ void __launch_bounds__(192, 1) k_small_tc(const __grid_constant__ TcP
     const int count = base + (c < rem ? 1 : 0);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < 3; ++i) {
             ptx::mbar_init(&x_full[i], 1);
             ptx::mbar_init(&x_empty[i], 1);
             ptx::mbar_init(&d1_full[i], 1);
-            ptx::mbar_init(&d2_full[i], 1);
-            ptx::mbar_init(&tmem_empty[i], 4);
         }
-        ptx::mbar_init(xlo_full, 4);
-        ptx::mbar_init(s_full, 4);
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&s_full[i], 8);
+            ptx::mbar_init(&d2_full[i], 1);
+            ptx::mbar_init(&d2_empty[i], 4);
+        }
+        ptx::mbar_init(xlo_full, 8);
         ptx::mbar_init(b_full, 1);
         ptx::mbar_init(drain, 1);
         ptx::fence_mbar_init();
     }
     if (warp == 1) {
-        ptx::tmem_alloc(tmem_slot, 256);
+        ptx::tmem_alloc(tmem_slot, 512);
         ptx::tmem_relinquish();
         ptx::tc_fence_before();
     }
@@ -145,8 +157,8 @@ __global__ void __launch_bounds__(192, 1) k_small_tc(const __grid_constant__ TcP
         if (lane == 0) {
             int issued = 0;
             for (int i = 0; i < count && ok; ++i) {
-                const int tile = t0 + i, s = i & 1;
-                if (!ptx::mbar_wait(&x_empty[s], ((i >> 1) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
+                const int tile = t0 + i, s = i % kStages;
+                if (!ptx::mbar_wait(&x_empty[s], ((i / kStages) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
                 const int sg = find_seg(P, tile);
                 const int row0 = (tile - P.seg[sg].tile_start) * kTcRows;
                 ptx::mbar_expect_tx(&x_full[s], kTileBytes);
@@ -157,8 +169,8 @@ __global__ void __launch_bounds__(192, 1) k_small_tc(const __grid_constant__ TcP
             if (!ok) {
                 atomicOr(P.err, kErrTimeout);
                 // let the loads already in flight land before the CTA exits
-                for (int i = max(0, issued - 2); i < issued; ++i)
-                    ptx::mbar_wait(&x_full[i & 1], (i >> 1) & 1, kWaitLimit);
+                for (int i = max(0, issued - kStages); i < issued; ++i)
+                    ptx::mbar_wait(&x_full[i % kStages], (i / kStages) & 1, kWaitLimit);
             }
         }
     } else if (warp == 1) {
@@ -166,84 +178,127 @@ __global__ void __launch_bounds__(192, 1) k_small_tc(const __grid_constant__ TcP
         if (lane == 0) {
             constexpr uint32_t idesc = ptx::idesc_tf32(128, 64);
             const uint32_t sB = ptx::smem_u32(Bimg), sX = ptx::smem_u32(xbuf),
-                           sXlo = ptx::smem_u32(xlo), sShi = ptx::smem_u32(Shi),
-                           sSlo = ptx::smem_u32(Slo);
+                           sXlo = ptx::smem_u32(xlo);
             const float* cur = nullptr;
             uint32_t nb = 0, nd = 0;
-            for (int i = 0; i < count && ok; ++i) {
-                const int tile = t0 + i, s = i & 1, b = i & 1;
-                const int sg = find_seg(P, tile);
-                if (P.images[sg] != cur) {
-                    if (i > 0) {  // all MMAs reading the old operands must finish first
-                        ptx::mma_commit(drain);
-                        if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) { ok = false; break; }
-                        ++nd;
-                    }
-                    ptx::mbar_expect_tx(b_full, 4 * kImgBytes);
-                    ptx::bulk_load(Bimg, P.images[sg], 4 * kImgBytes, b_full);
-                    if (!ptx::mbar_wait(b_full, nb & 1, kWaitLimit)) { ok = false; break; }
-                    ++nb;
-                    cur = P.images[sg];
+            int last2 = -1;  // last tile whose Cauchy GEMM was issued
+            int done2 = -1;  // every Cauchy GEMM up to this tile is known complete
+
+            // make the operand images of tile i's plan resident (drains the tensor pipe first)
+            auto ensure_plan = [&](int i) -> bool {
+                const float* img = P.images[find_seg(P, t0 + i)];
+                if (img == cur) return true;
+                if (cur) {
+                    ptx::mma_commit(drain);
+                    if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) return false;
+                    ++nd;
+                    done2 = last2;
                 }
-                if (!ptx::mbar_wait(&tmem_empty[b], ((i >> 1) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
-                if (!ptx::mbar_wait(xlo_full, i & 1, kWaitLimit)) { ok = false; break; }
+                ptx::mbar_expect_tx(b_full, 4 * kImgBytes);
+                ptx::bulk_load(Bimg, img, 4 * kImgBytes, b_full);
+                if (!ptx::mbar_wait(b_full, nb & 1, kWaitLimit)) return false;
+                ++nb;
+                cur = img;
+                return true;
+            };
+            // S = X B1^T for tile i: corrections first, hi*hi last
+            auto mma1 = [&](int i) -> bool {
+                const int s = i % kStages, d = i % 3;
+                // D1[d] was the hi operand of the Cauchy GEMM of tile i - 3. In
+                // issue order that GEMM's d2_full phase is the latest one of its
+                // buffer, except after a plan switch, whose drain already
+                // completed it (and may have completed one more phase).
+                if (i >= 3 && done2 < i - 3) {
+                    if (!ptx::mbar_wait(&d2_full[(i - 3) & 1], ((i - 3) >> 1) & 1, kWaitLimit)) return false;
+                    done2 = i - 3;
+                }
+                if (!ptx::mbar_wait(xlo_full, i & 1, kWaitLimit)) return false;
                 ptx::tc_fence_after();
-                const uint32_t d1 = tmem + b * 128, d2 = d1 + 64;
+                const uint32_t d1 = tmem + kColD1 + d * 64;
                 const uint32_t sA = sX + s * kTileBytes;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const uint32_t ka = (k >> 2) * (kTileBytes / 2) + (k & 3) * 32;
-                    const uint32_t kbb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    const uint64_t ah = ptx::desc_sw128(sA + ka), al = ptx::desc_sw128(sXlo + ka);
-                    const uint64_t bh = ptx::desc_sw128(sB + 0 * kImgBytes + kbb);
-                    const uint64_t bl = ptx::desc_sw128(sB + 1 * kImgBytes + kbb);
-                    ptx::mma_tf32(d1, ah, bh, idesc, k > 0);
-                    ptx::mma_tf32(d1, ah, bl, idesc, 1);
-                    ptx::mma_tf32(d1, al, bh, idesc, 1);
+                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
+                    ptx::mma_tf32(d1, ptx::desc_sw128(sA + ka), ptx::desc_sw128(sB + 1 * kImgBytes + kb), idesc, k > 0);
                 }
-                ptx::mma_commit(&x_empty[s]);
-                ptx::mma_commit(&d1_full[b]);
-                if (!ptx::mbar_wait(s_full, i & 1, kWaitLimit)) { ok = false; break; }
-                ptx::tc_fence_after();
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const uint32_t ka = (k >> 2) * (kTileBytes / 2) + (k & 3) * 32;
-                    const uint32_t kbb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    const uint64_t ah = ptx::desc_sw128(sShi + ka), al = ptx::desc_sw128(sSlo + ka);
-                    const uint64_t bh = ptx::desc_sw128(sB + 2 * kImgBytes + kbb);
-                    const uint64_t bl = ptx::desc_sw128(sB + 3 * kImgBytes + kbb);
-                    ptx::mma_tf32(d2, ah, bh, idesc, k > 0);
-                    ptx::mma_tf32(d2, ah, bl, idesc, 1);
-                    ptx::mma_tf32(d2, al, bh, idesc, 1);
+                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
+                    ptx::mma_tf32(d1, ptx::desc_sw128(sXlo + ka), ptx::desc_sw128(sB + 0 * kImgBytes + kb), idesc, 1);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t ka = (k >> 2) * (kTileBytes / 2) + (k & 3) * 32;
+                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
+                    ptx::mma_tf32(d1, ptx::desc_sw128(sA + ka), ptx::desc_sw128(sB + 0 * kImgBytes + kb), idesc, 1);
+                }
+                ptx::mma_commit(&x_empty[s]);
+                ptx::mma_commit(&d1_full[d]);
+                return true;
+            };
+            // Y = S B2^T for tile i: S hi straight from the D1 accumulator, S_lo from TMEM
+            auto mma2 = [&](int i) -> bool {
+                const int b = i & 1;
+                if (!ptx::mbar_wait(&s_full[b], (i >> 1) & 1, kWaitLimit)) return false;
+                if (!ptx::mbar_wait(&d2_empty[b], ((i >> 1) & 1) ^ 1, kWaitLimit)) return false;
+                ptx::tc_fence_after();
+                const uint32_t d2 = tmem + kColD2 + b * 64;
+                const uint32_t sh = tmem + kColD1 + (i % 3) * 64, sl = tmem + kColSlo + b * 64;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
+                    ptx::mma_tf32_ts(d2, sh + 8 * k, ptx::desc_sw128(sB + 3 * kImgBytes + kb), idesc, k > 0);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
+                    ptx::mma_tf32_ts(d2, sl + 8 * k, ptx::desc_sw128(sB + 2 * kImgBytes + kb), idesc, 1);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
+                    ptx::mma_tf32_ts(d2, sh + 8 * k, ptx::desc_sw128(sB + 2 * kImgBytes + kb), idesc, 1);
                 }
                 ptx::mma_commit(&d2_full[b]);
+                last2 = i;
+                return true;
+            };
+
+            if (count > 0) ok = ensure_plan(0) && mma1(0);
+            for (int i = 0; i < count && ok; ++i) {
+                if (i + 1 < count) {
+                    const bool same = P.images[find_seg(P, t0 + i + 1)] == cur;
+                    if (same) ok = mma1(i + 1) && mma2(i);
+                    else ok = mma2(i) && ensure_plan(i + 1) && mma1(i + 1);
+                } else {
+                    ok = mma2(i);
+                }
             }
             // every MMA done before TMEM is released
             ptx::mma_commit(drain);
             if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) ok = false;
             if (!ok) atomicOr(P.err, kErrTimeout);
         }
-    } else {
-        // ------------------------------------------------------------ epilogue
-        const int etid = threadIdx.x - 64;  // 0..127
-        const int q = warp & 3;             // TMEM lane quarter this warp may access
-        const int r = 32 * q + lane;        // tile row = TMEM lane
-        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-        float v[64];
+    } else if (warp < 10) {
+        // ------------------------------------------- x_lo and S_lo (8 warps)
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2;          // column half: K-block h of the tile
+        const int r = 32 * q + lane;            // tile row = TMEM lane
+        const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        uint32_t u[32];
 
         auto conv = [&](int i) -> bool {
-            const int s = i & 1;
-            if (!ptx::mbar_wait(&x_full[s], (i >> 1) & 1, kWaitLimit)) return false;
+            const int s = i % kStages;
+            if (!ptx::mbar_wait(&x_full[s], (i / kStages) & 1, kWaitLimit)) return false;
             const unsigned char* src = xbuf + s * kTileBytes;
-            for (int off = etid * 16; off < (int)kTileBytes; off += 128 * 16) {
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                const uint32_t off = sw128_off(r, 8 * h + cc);
                 float4 a = *reinterpret_cast<const float4*>(src + off);
-                float4 lo;
-                // the MMA reads x truncated to TF32; x_lo carries the rest, rounded to TF32
-                lo.x = ptx::tf32_round(a.x - __uint_as_float(__float_as_uint(a.x) & ~0x1FFFu));
-                lo.y = ptx::tf32_round(a.y - __uint_as_float(__float_as_uint(a.y) & ~0x1FFFu));
-                lo.z = ptx::tf32_round(a.z - __uint_as_float(__float_as_uint(a.z) & ~0x1FFFu));
-                lo.w = ptx::tf32_round(a.w - __uint_as_float(__float_as_uint(a.w) & ~0x1FFFu));
-                *reinterpret_cast<float4*>(xlo + off) = lo;
+                *reinterpret_cast<uint4*>(xlo + off) =
+                    make_uint4(lo_tf32(a.x), lo_tf32(a.y), lo_tf32(a.z), lo_tf32(a.w));
             }
             ptx::fence_proxy_async_smem();
             __syncwarp();
@@ -253,54 +308,93 @@ __global__ void __launch_bounds__(192, 1) k_small_tc(const __grid_constant__ TcP
 
         if (count > 0) ok = conv(0);
         for (int i = 0; i < count && ok; ++i) {
+            const int b = i & 1, d = i % 3;
+            if (!ptx::mbar_wait(&d1_full[d], (i / 3) & 1, kWaitLimit)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t dcol = tmem + lanes + kColD1 + d * 64 + 32 * h;
+            ptx::tmem_ld16(dcol, *reinterpret_cast<uint32_t(*)[16]>(u));
+            ptx::tmem_ld16(dcol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
+            // the DCT GEMM of tile i is done: x_lo is free for tile i + 1
+            if (i + 1 < count && !conv(i + 1)) { ok = false; break; }
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) u[j] = lo_tf32(__uint_as_float(u[j]));
+            const uint32_t scol = tmem + lanes + kColSlo + b * 64 + 32 * h;
+            ptx::tmem_st16(scol, *reinterpret_cast<uint32_t(*)[16]>(u));
+            ptx::tmem_st16(scol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
+            ptx::tmem_wait_st();
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&s_full[b]);
+        }
+        if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
+    } else if (warp < 14) {
+        // ------------------------------------------------- Y out (4 warps)
+        const int q = warp & 3;
+        const int r = 32 * q + lane;
+        const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        const int gtid = threadIdx.x - 320;     // 0..127
+        uint32_t u[64];
+        for (int i = 0; i < count && ok; ++i) {
             const int tile = t0 + i, b = i & 1;
             const int sg = find_seg(P, tile);
             const int row0 = (tile - P.seg[sg].tile_start) * kTcRows;
-            // S = D1: split into TF32 hi / lo operand tiles
-            if (!ptx::mbar_wait(&d1_full[b], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
-            ptx::tc_fence_after();
-            if (etid == 0) ptx::bulk_wait_group_read0();  // previous Y store has read its staging
-            ptx::named_bar_sync(1, 128);
-            load_tmem_row64(tmem + lane_off + b * 128, v);
-            {
-                float lo[64];
-#pragma unroll
-                for (int e = 0; e < 64; ++e) {
-                    float h = ptx::tf32_round(v[e]);
-                    lo[e] = ptx::tf32_round(v[e] - h);
-                    v[e] = h;
-                }
-                store_row_sw128(Shi, r, v);
-                store_row_sw128(Slo, r, lo);
-            }
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(s_full);
-            if (i + 1 < count && !conv(i + 1)) { ok = false; break; }
-            // Y = D2: stage in shared memory, store with TMA
             if (!ptx::mbar_wait(&d2_full[b], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
             ptx::tc_fence_after();
-            load_tmem_row64(tmem + lane_off + b * 128 + 64, v);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                ptx::tmem_ld16(tmem + lanes + kColD2 + b * 64 + 16 * j, *reinterpret_cast<uint32_t(*)[16]>(u + 16 * j));
+            ptx::tmem_wait_ld();
             ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&tmem_empty[b]);
-            store_row_sw128(Shi, r, v);
+            if (lane == 0) ptx::mbar_arrive(&d2_empty[b]);
+            if (gtid == 0) ptx::bulk_wait_group_read0();  // previous Y store has read the staging
+            ptx::named_bar_sync(2, 128);
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc)
+                *reinterpret_cast<uint4*>(ybuf + sw128_off(r, cc)) =
+                    make_uint4(u[4 * cc], u[4 * cc + 1], u[4 * cc + 2], u[4 * cc + 3]);
             ptx::fence_proxy_async_smem();
-            ptx::named_bar_sync(1, 128);
-            if (etid == 0) {
-                ptx::tma_store_2d(&P.ymap[sg], 0, row0, Shi);
-                ptx::tma_store_2d(&P.ymap[sg], 32, row0, Shi + kTileBytes / 2);
+            ptx::named_bar_sync(2, 128);
+            if (gtid == 0) {
+                ptx::tma_store_2d(&P.ymap[sg], 0, row0, ybuf);
+                ptx::tma_store_2d(&P.ymap[sg], 32, row0, ybuf + kTileBytes / 2);
                 ptx::bulk_commit_group();
             }
         }
-        if (etid == 0) ptx::bulk_wait_group0();
+        if (gtid == 0) ptx::bulk_wait_group0();
         if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
+    } else {
+        // ------------------------------------------- leftover signals (warp 14)
+        // y = W (U^T x) per signal: lanes own output coefficients k, k + 32
+        for (int sg = c; sg < P.nseg; sg += G) {
+            const TcSeg& S = P.seg[sg];
+            const int n = S.n;
+            for (int t = 0; t < S.tail; ++t) {
+                const float* xs = S.xt + (int64_t)t * n;
+                float s0 = 0.f, s1 = 0.f;
+                for (int j = 0; j < n; ++j) {
+                    const float xj = xs[j];
+                    if (lane < n) s0 = fmaf(S.ct[lane * n + j], xj, s0);
+                    if (lane + 32 < n) s1 = fmaf(S.ct[(lane + 32) * n + j], xj, s1);
+                }
+                float y0 = 0.f, y1 = 0.f;
+                for (int k = 0; k < n; ++k) {
+                    const float sk = __shfl_sync(0xffffffffu, k < 32 ? s0 : s1, k & 31);
+                    if (lane < n) y0 = fmaf(S.w[lane * n + k], sk, y0);
+                    if (lane + 32 < n) y1 = fmaf(S.w[(lane + 32) * n + k], sk, y1);
+                }
+                float* ys = S.yt + (int64_t)t * n;
+                if (lane < n) ys[lane] = y0;
+                if (lane + 32 < n) ys[lane + 32] = y1;
+            }
+        }
     }
 
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (warp == 1) ptx::tmem_dealloc(tmem, 256);
+    if (warp == 1) ptx::tmem_dealloc(tmem, 512);
 }
 
 // --------------------------------------------------------- operand images
@@ -338,7 +432,9 @@ dctplus_status setup_small_tc(dctplus_plan_t p) {
     return DCTPLUS_OK;
 }
 
-bool small_tc_capable(dctplus_plan_t p) { return tc_size(p->n) && p->tc.images != nullptr; }
+bool small_tc_capable(dctplus_plan_t p) {
+    return tc_size(p->n) && p->tc.images != nullptr && p->d_ct32 && p->d_w32;
+}
 
 // ------------------------------------------------------------- host launch
 
@@ -381,8 +477,9 @@ static int sm_count_tc(int dev) {
     return cached[d];
 }
 
-// Launches the tensor-core kernel over packed-row segments. x/y of every
-// segment must be 16-byte aligned; rows64 = number of full 64-sample rows.
+// Launches the tensor-core kernel over segments of whole signals. x and y of
+// every segment must be 16-byte aligned. Full packed rows go to the tensor
+// cores; the leftover signals of each segment to the kernel's CUDA-core warp.
 dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream_t s, int dev) {
     static bool attr[64] = {};
     if (!attr[dev & 63]) {
@@ -393,24 +490,36 @@ dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream
     while (i0 < segs.size()) {
         TcParams P;
         memset(&P, 0, sizeof(P));
-        int tiles = 0, ns = 0;
+        int tiles = 0, ns = 0, tails = 0;
         for (; i0 < segs.size() && ns < kTcMaxSeg; ++i0) {
             const TcSegHost& g = segs[i0];
-            if (g.rows64 <= 0) continue;
-            if (!encode_map(&P.xmap[ns], g.x, g.rows64) || !encode_map(&P.ymap[ns], g.y, g.rows64))
+            const int n = g.plan->n;
+            const int64_t rows64 = g.rows * n / 64;
+            const int64_t body = rows64 * 64 / n;
+            if (g.rows <= 0) continue;
+            if (rows64 > 0 && (!encode_map(&P.xmap[ns], g.x, rows64) || !encode_map(&P.ymap[ns], g.y, rows64)))
                 return DCTPLUS_ERR_CUDA;
             P.images[ns] = g.plan->tc.images;
-            P.seg[ns].tile_start = tiles;
-            P.seg[ns].rows64 = (int)g.rows64;
-            tiles += (int)((g.rows64 + kTcRows - 1) / kTcRows);
+            TcSeg& t = P.seg[ns];
+            t.tile_start = tiles;
+            t.rows64 = (int)rows64;
+            t.n = n;
+            t.tail = (int)(g.rows - body);
+            t.xt = g.x + body * n;
+            t.yt = g.y + body * n;
+            t.ct = g.plan->d_ct32;
+            t.w = g.plan->d_w32;
+            tiles += (int)((rows64 + kTcRows - 1) / kTcRows);
+            tails += t.tail > 0;
             ++ns;
         }
         if (ns == 0) continue;
         P.nseg = ns;
         P.ntiles = tiles;
         P.err = device_error_word(dev);
-        int grid = std::min(tiles, sm_count_tc(dev));
-        k_small_tc<<<grid, 192, kSmemBytes, s>>>(P);
+        int grid = std::min(std::max(tiles, tails > 0 ? ns : 0), sm_count_tc(dev));
+        if (grid <= 0) continue;
+        k_small_tc<<<grid, kTcThreads, kSmemBytes, s>>>(P);
         count_launch();
         DCTPLUS_CUDA_TRY(cudaGetLastError());
     }
@@ -421,23 +530,15 @@ static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 
 
 bool small_tc_available(dctplus_plan_t p) { return small_tc_capable(p); }
 
-// One plan: the packed body goes to the tensor cores, the < 64/n leftover
-// signals to the CUDA-core kernel.
+// One plan over a contiguous batch: one launch of the tensor-core kernel.
 dctplus_status launch_small_tc(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
                                int64_t ldy, int64_t batch, cudaStream_t s) {
     const int n = p->n;
     if (!small_tc_capable(p) || ldx != n || ldy != n || !aligned16(x) || !aligned16(y))
         return launch_small_simt_f32(p, x, ldx, y, ldy, batch, s);
-    const int64_t rows64 = batch * n / 64;
-    const int64_t body = rows64 * 64 / n;  // signals in full packed rows
-    if (rows64 > 0) {
-        std::vector<TcSegHost> segs = {{p, x, y, rows64}};
-        dctplus_status st = launch_tc_segments(segs, s, p->device);
-        if (st != DCTPLUS_OK) return st;
-    }
-    if (batch > body)
-        return launch_small_simt_f32(p, x + body * n, n, y + body * n, n, batch - body, s);
-    return DCTPLUS_OK;
+    if (batch <= 0) return DCTPLUS_OK;
+    std::vector<TcSegHost> segs = {{p, x, y, batch}};
+    return launch_tc_segments(segs, s, p->device);
 }
 
 }  // namespace dctplus

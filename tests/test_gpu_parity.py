@@ -220,6 +220,7 @@ def test_mixed_size_group_matches_oracle(pkg):
     # host-buffer variant gives the same bytes
     yh = group.forward_host(wl.x, seg)
     assert np.array_equal(yh, y.astype(np.float32))
+    assert pkg.dctplus_sync_check(0) == 0
     group.close()
     for p in plans:
         p.close()
@@ -242,6 +243,7 @@ def test_mixed_size_full_workload_sampled(pkg):
         got = y[s.offset:s.offset + s.rows * s.n].reshape(s.rows, s.n)[rows].astype(np.float64)
         nz = np.linalg.norm(ref, axis=1) > 0
         assert relerr(got[nz], ref[nz]).max() < F32_TOL, (s.n, s.update)
+    assert pkg.dctplus_sync_check(0) == 0
     group.close()
     for p in plans:
         p.close()
