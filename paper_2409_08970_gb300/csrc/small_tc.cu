@@ -17,16 +17,24 @@
 // and the hi*hi terms last: the large partial sums see 8 roundings, not 24.
 //
 // Pipeline: the DCT GEMM of tile t+1 is issued before the Cauchy GEMM of tile
-// t, so it runs while the epilogue forms tile t's S_lo.
+// t, so it runs while the epilogue forms tile t's S_lo; x_lo is double
+// buffered, so x_lo of tile t+1 is formed while the DCT GEMM of tile t runs.
+// Shared memory holds the plan's operand images and a 4-stage ring of x tiles
+// (a stage is held from its TMA load until the DCT GEMM has read it, so the
+// ring depth bounds the loads in flight); all A-side operands the epilogue
+// forms live in TMEM.
 // Roles (480 threads, one persistent CTA per SM):
-//   warp 0       TMA producer: x tiles into a 3-stage ring (128-byte swizzle)
+//   warp 0       TMA producer: x tiles into a 4-stage ring (128-byte swizzle)
 //   warp 1       TMEM owner and MMA issuer (one thread)
-//   warps 2..9   x_lo into shared memory; S_lo from the S accumulator into
-//                TMEM; two warps per TMEM lane quarter, 32 columns each
+//   warps 2..9   x_lo and S_lo into TMEM; two warps per TMEM lane quarter,
+//                32 columns each
 //   warps 10..13 Y (TMEM) staged in shared memory and stored by TMA
 //   warp 14      the < 64/n signals of each segment that do not fill a packed
 //                row, on CUDA cores from the plan's FP32 tables
-// TMEM columns: D1[3] 0..191, D2[2] 192..319, S_lo[2] 320..447.
+// TMEM columns: D1[3] 0..191, D2 192..255, S_lo[2] 256..383, x_lo[2] 384..511.
+// (The Y accumulator D2 is single buffered: its reader drains it right after
+// each Cauchy GEMM; S_lo and x_lo are double buffered so that neither GEMM
+// waits on the other's previous tile.)
 // Every mbarrier wait is bounded; a wait that runs out sets the device error
 // word and the CTA winds down (no trap, TMEM released).
 #include <cudaTypedefs.h>
@@ -42,7 +50,7 @@ namespace dctplus {
 
 constexpr int kTcMaxSeg = 40;
 constexpr int kTcRows = 128;
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kTcThreads = 480;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -51,13 +59,12 @@ constexpr uint32_t kImgBytes = 16384;               // one 64x64 TF32 operand im
 constexpr uint32_t kTileBytes = kTcRows * 64 * 4;   // 32 KB
 constexpr uint32_t kOffB = 0;                       // B1 hi, B1 lo, B2 hi, B2 lo
 constexpr uint32_t kOffX = 4 * kImgBytes;           // kStages x 32 KB
-constexpr uint32_t kOffXlo = kOffX + kStages * kTileBytes;
-constexpr uint32_t kOffY = kOffXlo + kTileBytes;
+constexpr uint32_t kOffY = kOffX + kStages * kTileBytes;
 constexpr uint32_t kOffBar = kOffY + kTileBytes;
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;  // + barriers + alignment slack
 
 // TMEM column map
-constexpr uint32_t kColD1 = 0, kColD2 = 192, kColSlo = 320;
+constexpr uint32_t kColD1 = 0, kColD2 = 192, kColSlo = 256, kColXlo = 384;
 
 struct TcSeg {
     int tile_start;     // first tile index of the segment in this launch
@@ -104,19 +111,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* Bimg = sm + kOffB;
     unsigned char* xbuf = sm + kOffX;
-    unsigned char* xlo = sm + kOffXlo;
     unsigned char* ybuf = sm + kOffY;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
-    uint64_t* x_full = bars + 0;    // [3]
-    uint64_t* x_empty = bars + 3;   // [3]
-    uint64_t* d1_full = bars + 6;   // [3]
-    uint64_t* s_full = bars + 9;    // [2]
-    uint64_t* d2_full = bars + 11;  // [2]
-    uint64_t* d2_empty = bars + 13; // [2]
-    uint64_t* xlo_full = bars + 15;
-    uint64_t* b_full = bars + 16;
-    uint64_t* drain = bars + 17;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 20);
+    uint64_t* x_full = bars + 0;     // [kStages]
+    uint64_t* x_empty = bars + 4;    // [kStages]
+    uint64_t* d1_full = bars + 8;    // [3] DCT GEMM of the tile in D1[d] done
+    uint64_t* d1_free = bars + 11;   // [3] Cauchy GEMM that read D1[d] done
+    uint64_t* s_full = bars + 14;    // [2] S_lo[b] written
+    uint64_t* xlo_full = bars + 16;  // [2] x_lo[b] written
+    uint64_t* d2_full = bars + 18;   // Cauchy GEMM of the tile in D2 done
+    uint64_t* d2_empty = bars + 19;  // D2 read out
+    uint64_t* b_full = bars + 20;
+    uint64_t* drain = bars + 21;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 24);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -127,17 +134,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
     const int count = base + (c < rem ? 1 : 0);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < kStages; ++i) {
             ptx::mbar_init(&x_full[i], 1);
             ptx::mbar_init(&x_empty[i], 1);
+        }
+        for (int i = 0; i < 3; ++i) {
             ptx::mbar_init(&d1_full[i], 1);
+            ptx::mbar_init(&d1_free[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&s_full[i], 8);
-            ptx::mbar_init(&d2_full[i], 1);
-            ptx::mbar_init(&d2_empty[i], 4);
+            ptx::mbar_init(&xlo_full[i], 8);
         }
-        ptx::mbar_init(xlo_full, 8);
+        ptx::mbar_init(d2_full, 1);
+        ptx::mbar_init(d2_empty, 4);
         ptx::mbar_init(b_full, 1);
         ptx::mbar_init(drain, 1);
         ptx::fence_mbar_init();
@@ -177,12 +187,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = ptx::idesc_tf32(128, 64);
-            const uint32_t sB = ptx::smem_u32(Bimg), sX = ptx::smem_u32(xbuf),
-                           sXlo = ptx::smem_u32(xlo);
+            // descriptors of the operand bases; a K step or another stage or
+            // image only moves the start address (field in 16-byte units)
+            const uint64_t dB0 = ptx::desc_sw128(ptx::smem_u32(Bimg));
+            const uint64_t dX0 = ptx::desc_sw128(ptx::smem_u32(xbuf));
+            // K step k = 8 TF32 = 32 bytes inside a 128-byte swizzle row; K
+            // block k / 4 is the next 128 (A tile) or 64 (B image) rows
+            auto kA16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kTileBytes / 32) + (k & 3) * 2); };
+            auto kB16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kImgBytes / 32) + (k & 3) * 2); };
             const float* cur = nullptr;
             uint32_t nb = 0, nd = 0;
-            int last2 = -1;  // last tile whose Cauchy GEMM was issued
-            int done2 = -1;  // every Cauchy GEMM up to this tile is known complete
 
             // make the operand images of tile i's plan resident (drains the tensor pipe first)
             auto ensure_plan = [&](int i) -> bool {
@@ -192,7 +206,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
                     ptx::mma_commit(drain);
                     if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) return false;
                     ++nd;
-                    done2 = last2;
                 }
                 ptx::mbar_expect_tx(b_full, 4 * kImgBytes);
                 ptx::bulk_load(Bimg, img, 4 * kImgBytes, b_full);
@@ -204,36 +217,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             // S = X B1^T for tile i: corrections first, hi*hi last
             auto mma1 = [&](int i) -> bool {
                 const int s = i % kStages, d = i % 3;
-                // D1[d] was the hi operand of the Cauchy GEMM of tile i - 3. In
-                // issue order that GEMM's d2_full phase is the latest one of its
-                // buffer, except after a plan switch, whose drain already
-                // completed it (and may have completed one more phase).
-                if (i >= 3 && done2 < i - 3) {
-                    if (!ptx::mbar_wait(&d2_full[(i - 3) & 1], ((i - 3) >> 1) & 1, kWaitLimit)) return false;
-                    done2 = i - 3;
-                }
-                if (!ptx::mbar_wait(xlo_full, i & 1, kWaitLimit)) return false;
+                // D1[d] was the hi operand of the Cauchy GEMM of tile i - 3
+                if (i >= 3 && !ptx::mbar_wait(&d1_free[d], ((i / 3) - 1) & 1, kWaitLimit)) return false;
+                if (!ptx::mbar_wait(&xlo_full[i & 1], (i >> 1) & 1, kWaitLimit)) return false;
                 ptx::tc_fence_after();
                 const uint32_t d1 = tmem + kColD1 + d * 64;
-                const uint32_t sA = sX + s * kTileBytes;
+                const uint64_t dA = dX0 + (uint64_t)(s * (kTileBytes >> 4));
+                const uint32_t xl = tmem + kColXlo + (i & 1) * 64;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t ka = (k >> 2) * (kTileBytes / 2) + (k & 3) * 32;
-                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    ptx::mma_tf32(d1, ptx::desc_sw128(sA + ka), ptx::desc_sw128(sB + 1 * kImgBytes + kb), idesc, k > 0);
-                }
+                for (int k = 0; k < 8; ++k)
+                    ptx::mma_tf32(d1, dA + kA16(k), dB0 + 1 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t ka = (k >> 2) * (kTileBytes / 2) + (k & 3) * 32;
-                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    ptx::mma_tf32(d1, ptx::desc_sw128(sXlo + ka), ptx::desc_sw128(sB + 0 * kImgBytes + kb), idesc, 1);
-                }
+                for (int k = 0; k < 8; ++k)
+                    ptx::mma_tf32_ts(d1, xl + 8 * k, dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t ka = (k >> 2) * (kTileBytes / 2) + (k & 3) * 32;
-                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    ptx::mma_tf32(d1, ptx::desc_sw128(sA + ka), ptx::desc_sw128(sB + 0 * kImgBytes + kb), idesc, 1);
-                }
+                for (int k = 0; k < 8; ++k)
+                    ptx::mma_tf32(d1, dA + kA16(k), dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
                 ptx::mma_commit(&x_empty[s]);
                 ptx::mma_commit(&d1_full[d]);
                 return true;
@@ -242,27 +241,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             auto mma2 = [&](int i) -> bool {
                 const int b = i & 1;
                 if (!ptx::mbar_wait(&s_full[b], (i >> 1) & 1, kWaitLimit)) return false;
-                if (!ptx::mbar_wait(&d2_empty[b], ((i >> 1) & 1) ^ 1, kWaitLimit)) return false;
+                if (!ptx::mbar_wait(d2_empty, (i & 1) ^ 1, kWaitLimit)) return false;
                 ptx::tc_fence_after();
-                const uint32_t d2 = tmem + kColD2 + b * 64;
+                const uint32_t d2 = tmem + kColD2;
                 const uint32_t sh = tmem + kColD1 + (i % 3) * 64, sl = tmem + kColSlo + b * 64;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    ptx::mma_tf32_ts(d2, sh + 8 * k, ptx::desc_sw128(sB + 3 * kImgBytes + kb), idesc, k > 0);
-                }
+                for (int k = 0; k < 8; ++k)
+                    ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 3 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    ptx::mma_tf32_ts(d2, sl + 8 * k, ptx::desc_sw128(sB + 2 * kImgBytes + kb), idesc, 1);
-                }
+                for (int k = 0; k < 8; ++k)
+                    ptx::mma_tf32_ts(d2, sl + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t kb = (k >> 2) * (kImgBytes / 2) + (k & 3) * 32;
-                    ptx::mma_tf32_ts(d2, sh + 8 * k, ptx::desc_sw128(sB + 2 * kImgBytes + kb), idesc, 1);
-                }
-                ptx::mma_commit(&d2_full[b]);
-                last2 = i;
+                for (int k = 0; k < 8; ++k)
+                    ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
+                ptx::mma_commit(d2_full);
+                ptx::mma_commit(&d1_free[i % 3]);
                 return true;
             };
 
@@ -295,37 +288,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             const unsigned char* src = xbuf + s * kTileBytes;
 #pragma unroll
             for (int cc = 0; cc < 8; ++cc) {
-                const uint32_t off = sw128_off(r, 8 * h + cc);
-                float4 a = *reinterpret_cast<const float4*>(src + off);
-                *reinterpret_cast<uint4*>(xlo + off) =
-                    make_uint4(lo_tf32(a.x), lo_tf32(a.y), lo_tf32(a.z), lo_tf32(a.w));
+                float4 a = *reinterpret_cast<const float4*>(src + sw128_off(r, 8 * h + cc));
+                u[4 * cc + 0] = lo_tf32(a.x);
+                u[4 * cc + 1] = lo_tf32(a.y);
+                u[4 * cc + 2] = lo_tf32(a.z);
+                u[4 * cc + 3] = lo_tf32(a.w);
             }
-            ptx::fence_proxy_async_smem();
+            const uint32_t xcol = tmem + lanes + kColXlo + (i & 1) * 64 + 32 * h;
+            ptx::tmem_st16(xcol, *reinterpret_cast<uint32_t(*)[16]>(u));
+            ptx::tmem_st16(xcol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
+            ptx::tmem_wait_st();
+            ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(xlo_full);
+            if (lane == 0) ptx::mbar_arrive(&xlo_full[i & 1]);
             return true;
         };
 
         if (count > 0) ok = conv(0);
         for (int i = 0; i < count && ok; ++i) {
-            const int b = i & 1, d = i % 3;
+            const int d = i % 3;
+            // x_lo buffer (i + 1) & 1 was read by the DCT GEMM of tile i - 1,
+            // complete since the previous iteration waited on it
+            if (i + 1 < count && !conv(i + 1)) { ok = false; break; }
             if (!ptx::mbar_wait(&d1_full[d], (i / 3) & 1, kWaitLimit)) { ok = false; break; }
             ptx::tc_fence_after();
             const uint32_t dcol = tmem + lanes + kColD1 + d * 64 + 32 * h;
             ptx::tmem_ld16(dcol, *reinterpret_cast<uint32_t(*)[16]>(u));
             ptx::tmem_ld16(dcol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
-            // the DCT GEMM of tile i is done: x_lo is free for tile i + 1
-            if (i + 1 < count && !conv(i + 1)) { ok = false; break; }
             ptx::tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 32; ++j) u[j] = lo_tf32(__uint_as_float(u[j]));
-            const uint32_t scol = tmem + lanes + kColSlo + b * 64 + 32 * h;
+            // S_lo[i & 1] was read by the Cauchy GEMM of tile i - 2, which was
+            // issued before the DCT GEMM of tile i: d1_full covers it
+            const uint32_t scol = tmem + lanes + kColSlo + (i & 1) * 64 + 32 * h;
             ptx::tmem_st16(scol, *reinterpret_cast<uint32_t(*)[16]>(u));
             ptx::tmem_st16(scol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
             ptx::tmem_wait_st();
             ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&s_full[b]);
+            if (lane == 0) ptx::mbar_arrive(&s_full[i & 1]);
         }
         if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
     } else if (warp < 14) {
@@ -336,18 +337,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         const int gtid = threadIdx.x - 320;     // 0..127
         uint32_t u[64];
         for (int i = 0; i < count && ok; ++i) {
-            const int tile = t0 + i, b = i & 1;
+            const int tile = t0 + i;
             const int sg = find_seg(P, tile);
             const int row0 = (tile - P.seg[sg].tile_start) * kTcRows;
-            if (!ptx::mbar_wait(&d2_full[b], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
+            if (!ptx::mbar_wait(d2_full, i & 1, kWaitLimit)) { ok = false; break; }
             ptx::tc_fence_after();
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                ptx::tmem_ld16(tmem + lanes + kColD2 + b * 64 + 16 * j, *reinterpret_cast<uint32_t(*)[16]>(u + 16 * j));
+                ptx::tmem_ld16(tmem + lanes + kColD2 + 16 * j, *reinterpret_cast<uint32_t(*)[16]>(u + 16 * j));
             ptx::tmem_wait_ld();
             ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&d2_empty[b]);
+            if (lane == 0) ptx::mbar_arrive(d2_empty);
             if (gtid == 0) ptx::bulk_wait_group_read0();  // previous Y store has read the staging
             ptx::named_bar_sync(2, 128);
 #pragma unroll
