@@ -61,12 +61,18 @@ typedef enum {
 
 typedef enum { DCTPLUS_F32 = 0, DCTPLUS_F64 = 1 } dctplus_dtype;
 
-/* How the Cauchy product of Theorem 3.1 is evaluated for FP32 data. */
+/* How the Cauchy product of Theorem 3.1 is evaluated for FP32 data with
+ * n > 64 (n <= 64 always runs the fused small-n kernels). */
 typedef enum {
-    DCTPLUS_CAUCHY_AUTO = 0,  /* pick by n (tuned crossover) */
-    DCTPLUS_CAUCHY_DENSE = 1, /* dense product, Cauchy tiles generated on chip */
+    DCTPLUS_CAUCHY_AUTO = 0,  /* pick by n */
+    DCTPLUS_CAUCHY_DENSE = 1, /* dense split-TF32 tensor-core product with the plan's
+                                 W = diag(a) C(mu, lambda) diag(z) table; n % 128 == 0, n <= 4096 */
     DCTPLUS_CAUCHY_HIER = 2,  /* O(n log n) hierarchical far-field expansion (Theorem 3.2) */
-    DCTPLUS_CAUCHY_SIMT = 3   /* plain CUDA-core product from a stored FP32 table (n <= 4096) */
+    DCTPLUS_CAUCHY_SIMT = 3,  /* CUDA-core product, W from a stored table (n <= 4096) or
+                                 generated tile by tile in shared memory */
+    DCTPLUS_CAUCHY_DENSE_GFT = 4 /* comparison baseline, not the factored method: one dense
+                                    tensor-core product with the full X^T (n % 128 == 0,
+                                    n <= 1024) */
 } dctplus_cauchy_mode;
 
 typedef struct {

@@ -27,6 +27,7 @@ CAUCHY_AUTO = 0
 CAUCHY_DENSE = 1
 CAUCHY_HIER = 2
 CAUCHY_SIMT = 3
+CAUCHY_DENSE_GFT = 4
 
 SEG_WORDS = 3
 

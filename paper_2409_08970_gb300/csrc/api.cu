@@ -118,7 +118,7 @@ dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, do
     dctplus_opts o{};
     o.device = -1;
     if (opts) o = *opts;
-    if (o.cauchy_mode < 0 || o.cauchy_mode > DCTPLUS_CAUCHY_SIMT || o.max_secular_iter < 0)
+    if (o.cauchy_mode < 0 || o.cauchy_mode > DCTPLUS_CAUCHY_DENSE_GFT || o.max_secular_iter < 0)
         return DCTPLUS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DCTPLUS_ERR_NO_DEVICE;
@@ -142,7 +142,6 @@ dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, do
         delete p;
         return st;
     }
-    if (p->cauchy_mode == DCTPLUS_CAUCHY_AUTO) p->cauchy_mode = DCTPLUS_CAUCHY_SIMT;
     *out = p;
     return DCTPLUS_OK;
 }

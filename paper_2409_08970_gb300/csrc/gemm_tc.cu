@@ -1,0 +1,256 @@
+// Split-TF32 tensor-core GEMM  Y[M x N] = A[M x K] * B[N x K]^T  (FP32 in/out).
+//
+// Used for the dense Cauchy product of Theorem 3.1 at large n (A = the DCT
+// coefficients s of a batch, B = W = X^T U from the plan, y = W s per signal)
+// and for the dense-GFT comparison (A = x, B = X^T).
+//
+// Each FP32 operand is hi + lo with hi, lo TF32: A_hi is A itself (the MMA
+// reads it truncated to TF32) and A_lo = rn_tf32(A - trunc_tf32(A)) is
+// supplied by the caller; B_hi, B_lo are both rounded (plan tables). A product
+// takes A_hi B_lo + A_lo B_hi (issued first) + A_hi B_hi.
+//
+// Accumulation: the MMA accumulates in FP32 rounding toward zero, which over
+// K = n (up to 4096) would bias results by many ulps. Each K chunk of 32 is
+// therefore accumulated in a fresh TMEM buffer (4 large-sum roundings) and the
+// epilogue warps add the chunk into FP32 registers with round-to-nearest.
+//
+// Tiles 128 x 128, persistent CTAs (one per SM), 448 threads:
+//   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo K-slices of 32 (3 stages)
+//   warp 1      TMEM owner (256 columns: two 128-column chunk buffers), MMA issuer
+//   warps 2..9  chunk promotion into registers, final store; two warps per
+//               TMEM lane quarter, 64 columns each
+// Bounded waits as in the small-n kernel.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace dctplus {
+
+namespace gemm {
+
+constexpr int kBM = 128, kBN = 128, kBK = 32;
+constexpr int kStages = 3;
+constexpr int kThreads = 320;
+constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kSlice = kBM * kBK * 4;           // 16 KB: one 128 x 32 FP32 slice
+constexpr uint32_t kStageBytes = 4 * kSlice;          // A_hi, A_lo, B_hi, B_lo
+constexpr uint32_t kOffBar = kStages * kStageBytes;
+constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;
+
+struct Params {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;  // A: [M x K], B: [N x K], FP32, box 32 x 128
+    float* y;
+    int64_t ldy;
+    int M, N, K;
+    int tiles_m, tiles_n;
+    unsigned* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ Params P) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
+    uint64_t* full = bars + 0;        // [kStages]
+    uint64_t* empty = bars + 4;       // [kStages]
+    uint64_t* acc_full = bars + 8;    // [2]
+    uint64_t* acc_empty = bars + 10;  // [2]
+    uint64_t* drain = bars + 12;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 16);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = P.tiles_m * P.tiles_n;
+    const int nk = P.K / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            ptx::mbar_init(&full[i], 1);
+            ptx::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&acc_full[i], 1);
+            ptx::mbar_init(&acc_empty[i], 8);
+        }
+        ptx::mbar_init(drain, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, 256);
+        ptx::tmem_relinquish();
+        ptx::tc_fence_before();
+    }
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0, issued = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int m0 = (t / P.tiles_n) * kBM, n0 = (t % P.tiles_n) * kBN;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kStages;
+                    if (!ptx::mbar_wait(&empty[s], ((it / kStages) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
+                    unsigned char* st = sm + s * kStageBytes;
+                    ptx::mbar_expect_tx(&full[s], kStageBytes);
+                    ptx::tma_load_2d(st + 0 * kSlice, &P.a_hi, kc * kBK, m0, &full[s]);
+                    ptx::tma_load_2d(st + 1 * kSlice, &P.a_lo, kc * kBK, m0, &full[s]);
+                    ptx::tma_load_2d(st + 2 * kSlice, &P.b_hi, kc * kBK, n0, &full[s]);
+                    ptx::tma_load_2d(st + 3 * kSlice, &P.b_lo, kc * kBK, n0, &full[s]);
+                    issued = it + 1;
+                }
+            }
+            if (!ok) {
+                atomicOr(P.err, kErrTimeout);
+                for (int i = max(0, issued - kStages); i < issued; ++i)
+                    ptx::mbar_wait(&full[i % kStages], (i / kStages) & 1, kWaitLimit);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = ptx::idesc_tf32(kBM, kBN);
+            const uint64_t d0 = ptx::desc_sw128(ptx::smem_u32(sm));
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kStages, b = it & 1;
+                    if (!ptx::mbar_wait(&acc_empty[b], ((it >> 1) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
+                    if (!ptx::mbar_wait(&full[s], (it / kStages) & 1, kWaitLimit)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t d = tmem + b * kBN;
+                    const uint64_t ds = d0 + (uint64_t)(s * (kStageBytes >> 4));
+                    const uint64_t ahi = ds, alo = ds + (kSlice >> 4), bhi = ds + 2 * (kSlice >> 4),
+                                   blo = ds + 3 * (kSlice >> 4);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) ptx::mma_tf32(d, ahi + 2 * k, blo + 2 * k, idesc, k > 0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) ptx::mma_tf32(d, alo + 2 * k, bhi + 2 * k, idesc, 1);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) ptx::mma_tf32(d, ahi + 2 * k, bhi + 2 * k, idesc, 1);
+                    ptx::mma_commit(&empty[s]);
+                    ptx::mma_commit(&acc_full[b]);
+                }
+            }
+            ptx::mma_commit(drain);
+            if (!ptx::mbar_wait(drain, 0, kWaitLimit)) ok = false;
+            if (!ok) atomicOr(P.err, kErrTimeout);
+        }
+    } else {
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int r = 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + 64 * h;
+        float acc[64];
+        uint32_t u[16];
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int m0 = (t / P.tiles_n) * kBM, n0 = (t % P.tiles_n) * kBN;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int b = it & 1;
+                if (!ptx::mbar_wait(&acc_full[b], (it >> 1) & 1, kWaitLimit)) { ok = false; break; }
+                ptx::tc_fence_after();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    ptx::tmem_ld16(tl + b * kBN + 16 * j, u);
+                    ptx::tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) acc[16 * j + e] += __uint_as_float(u[e]);
+                }
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&acc_empty[b]);
+            }
+            if (!ok) break;
+            const int row = m0 + r;
+            if (row < P.M) {
+                float* yr = P.y + (int64_t)row * P.ldy + n0 + 64 * h;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    reinterpret_cast<float4*>(yr)[j] =
+                        make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+            }
+        }
+        if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 1) ptx::tmem_dealloc(tmem, 256);
+}
+
+}  // namespace gemm
+
+// ----------------------------------------------------------------- host
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn_g() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &f, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// rows x cols FP32 row-major (leading dimension ld floats), box 32 x 128, 128-byte swizzle
+static bool encode_rows(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld) {
+    auto fn = encode_fn_g();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// y[M x N] = (a_hi + a_lo) (b_hi + b_lo)^T; K % 32 == 0, N % 128 == 0, 16-byte
+// aligned bases, leading dimensions multiples of 4 floats.
+dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda, const float* b_hi,
+                              const float* b_lo, int64_t ldb, float* y, int64_t ldy, int M, int N,
+                              int K, cudaStream_t s, int dev) {
+    if (M <= 0) return DCTPLUS_OK;
+    if (K % gemm::kBK || N % gemm::kBN || (lda & 3) || (ldb & 3) || (ldy & 3))
+        return DCTPLUS_ERR_UNSUPPORTED;
+    static bool attr[64] = {};
+    if (!attr[dev & 63]) {
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(gemm::k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)gemm::kSmemBytes));
+        attr[dev & 63] = true;
+    }
+    gemm::Params P;
+    memset(&P, 0, sizeof(P));
+    if (!encode_rows(&P.a_hi, a_hi, M, K, lda) || !encode_rows(&P.a_lo, a_lo, M, K, lda) ||
+        !encode_rows(&P.b_hi, b_hi, N, K, ldb) || !encode_rows(&P.b_lo, b_lo, N, K, ldb))
+        return DCTPLUS_ERR_CUDA;
+    P.y = y;
+    P.ldy = ldy;
+    P.M = M;
+    P.N = N;
+    P.K = K;
+    P.tiles_m = (M + gemm::kBM - 1) / gemm::kBM;
+    P.tiles_n = N / gemm::kBN;
+    P.err = device_error_word(dev);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = std::min(P.tiles_m * P.tiles_n, std::max(sms, 1));
+    gemm::k_gemm_tc<<<grid, gemm::kThreads, gemm::kSmemBytes, s>>>(P);
+    count_launch();
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+}  // namespace dctplus

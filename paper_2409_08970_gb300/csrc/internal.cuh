@@ -64,6 +64,10 @@ struct dctplus_plan_s {
     float* d_w32 = nullptr;        // n x n, W = X^T U row-major (n <= 4096)
     double* d_w64 = nullptr;       // n x n (F64 path, n <= 1024)
     float* d_twiddle = nullptr;    // FFT DCT tables (n >= 128)
+    float* d_whi = nullptr;        // n x n W split into TF32 hi / lo (dense tensor-core mode)
+    float* d_wlo = nullptr;
+    float* d_xthi = nullptr;       // n x n X^T split into TF32 hi / lo (dense-GFT baseline)
+    float* d_xtlo = nullptr;
     // per-row generator data for on-chip Cauchy tiles (FP32): pole, tau, -a
     int* d_gen_pole = nullptr;
     float* d_gen_tau = nullptr;
@@ -125,7 +129,7 @@ dctplus_status launch_small_simt_f64(dctplus_plan_t p, const double* x, int64_t 
 
 // large.cu
 dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
-                              int64_t lds, int64_t batch, cudaStream_t st);
+                              float* s_lo, int64_t lds, int64_t batch, cudaStream_t st);
 dctplus_status launch_cauchy_simt(dctplus_plan_t p, const float* s_in, int64_t lds, float* y,
                                   int64_t ldy, int64_t batch, cudaStream_t st);
 dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,

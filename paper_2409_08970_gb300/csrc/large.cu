@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace dctplus {
 
@@ -61,9 +62,16 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// One CTA per signal (grid-stride over the batch).
+// TF32 remainder of v for the split-TF32 contractions: rn_tf32(v - trunc_tf32(v))
+__device__ __forceinline__ float tf32_lo(float v) {
+    return __uint_as_float(ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu)));
+}
+
+// One CTA per signal (grid-stride over the batch). With s_lo non-null the
+// TF32 remainder of every coefficient is written there too (same layout).
 __global__ void __launch_bounds__(512) k_dct_fft(int n, const float* __restrict__ x, int64_t ldx,
-                                                 float* __restrict__ s, int64_t lds, int64_t batch,
+                                                 float* __restrict__ s, float* __restrict__ s_lo,
+                                                 int64_t lds, int64_t batch,
                                                  const float2* __restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = n / 2;
@@ -109,21 +117,24 @@ __global__ void __launch_bounds__(512) k_dct_fft(int n, const float* __restrict_
             float2 t = cmul(tw_split[k], fo);
             vk.x += t.x; vk.y += t.y;
             float2 bq = cmul(tw_post[k], vk);  // c_k exp(-i pi k/2n) V_k
-            if (k == 0) {
-                ss[0] = bq.x;
-            } else if (k == M) {
-                ss[M] = bq.x;
+            if (k == 0 || k == M) {
+                ss[k] = bq.x;
+                if (s_lo) s_lo[sig * lds + k] = tf32_lo(bq.x);
             } else {
                 ss[k] = bq.x;
                 // X_{n-k} = -Im(exp(-i pi k/2n) V_k); c_{n-k} = c_k for k > 0
                 ss[n - k] = -bq.y;
+                if (s_lo) {
+                    s_lo[sig * lds + k] = tf32_lo(bq.x);
+                    s_lo[sig * lds + n - k] = tf32_lo(-bq.y);
+                }
             }
         }
     }
 }
 
 dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
-                              int64_t lds, int64_t batch, cudaStream_t st) {
+                              float* s_lo, int64_t lds, int64_t batch, cudaStream_t st) {
     int n = p->n;
     if (!p->d_twiddle) return DCTPLUS_ERR_UNSUPPORTED;
     size_t smem = sizeof(float2) * n;  // two buffers of n/2
@@ -136,7 +147,7 @@ dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, flo
     int64_t grid = std::min<int64_t>(batch, 152 * std::max(1, (int)(200 * 1024 / std::max<size_t>(smem, 1)) ));
     grid = std::min<int64_t>(grid, 65535 * 16);
     if (grid <= 0) return DCTPLUS_OK;
-    k_dct_fft<<<(unsigned)grid, threads, smem, st>>>(n, x, ldx, s_out, lds, batch,
+    k_dct_fft<<<(unsigned)grid, threads, smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch,
                                                      reinterpret_cast<const float2*>(p->d_twiddle));
     count_launch();
     DCTPLUS_CUDA_TRY(cudaGetLastError());
@@ -290,16 +301,57 @@ dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, 
     return DCTPLUS_OK;
 }
 
-// Per-stream scratch for the DCT output s (batch x n floats).
+// hi copy and TF32 remainder of a row-major batch (dense-GFT baseline input)
+__global__ void k_split_rows(const float* __restrict__ x, int64_t ldx, int n, int64_t batch,
+                             float* __restrict__ hi, float* __restrict__ lo) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = batch * n;
+    for (; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = idx / n;
+        int j = (int)(idx % n);
+        float v = x[b * ldx + j];
+        hi[idx] = v;
+        lo[idx] = tf32_lo(v);
+    }
+}
+
+// Per-stream scratch for the DCT output (batch x n floats, twice for split operands).
 void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes);
+
+dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda, const float* b_hi,
+                              const float* b_lo, int64_t ldb, float* y, int64_t ldy, int M, int N,
+                              int K, cudaStream_t s, int dev);  // gemm_tc.cu
 
 dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
                                 int64_t ldy, int64_t batch, cudaStream_t st) {
-    int n = p->n;
+    const int n = p->n;
+    if (batch > INT32_MAX) return DCTPLUS_ERR_UNSUPPORTED;
+    const bool y_ok = (reinterpret_cast<uintptr_t>(y) & 15) == 0 && (ldy & 3) == 0;
+    const size_t plane = (size_t)batch * n;
+    if (p->cauchy_mode == DCTPLUS_CAUCHY_DENSE_GFT && y_ok) {
+        // comparison baseline: y = (x_hi + x_lo)(X^T_hi + X^T_lo)^T in one dense product
+        float* ws = static_cast<float*>(plan_workspace(p, st, 2 * sizeof(float) * plane));
+        if (!ws) return DCTPLUS_ERR_CUDA;
+        int64_t blocks = std::min<int64_t>((int64_t)((plane + 255) / 256), 152 * 16);
+        k_split_rows<<<(unsigned)blocks, 256, 0, st>>>(x, ldx, n, batch, ws, ws + plane);
+        count_launch();
+        DCTPLUS_CUDA_TRY(cudaGetLastError());
+        return launch_gemm_tc(ws, ws + plane, n, p->d_xthi, p->d_xtlo, n, y, ldy, (int)batch, n, n,
+                              st, p->device);
+    }
     if (n & (n - 1)) return DCTPLUS_ERR_UNSUPPORTED;
-    float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * (size_t)batch * n));
+    if (p->cauchy_mode == DCTPLUS_CAUCHY_DENSE && p->d_whi && y_ok) {
+        // Algorithm 1 steps 1-2 (DCT-II, split for the tensor cores), then y = W s
+        float* ws = static_cast<float*>(plan_workspace(p, st, 2 * sizeof(float) * plane));
+        if (!ws) return DCTPLUS_ERR_CUDA;
+        dctplus_status r = launch_dct_fft(p, x, ldx, ws, ws + plane, n, batch, st);
+        if (r != DCTPLUS_OK) return r;
+        return launch_gemm_tc(ws, ws + plane, n, p->d_whi, p->d_wlo, n, y, ldy, (int)batch, n, n,
+                              st, p->device);
+    }
+    float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * plane));
     if (!ws) return DCTPLUS_ERR_CUDA;
-    dctplus_status r = launch_dct_fft(p, x, ldx, ws, n, batch, st);
+    dctplus_status r = launch_dct_fft(p, x, ldx, ws, nullptr, n, batch, st);
     if (r != DCTPLUS_OK) return r;
     return launch_cauchy_simt(p, ws, n, y, ldy, batch, st);
 }

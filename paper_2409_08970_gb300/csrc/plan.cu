@@ -14,6 +14,7 @@
 #include <numeric>
 
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace dctplus {
 
@@ -188,10 +189,17 @@ __global__ void k_secular(int n, double rho, int K, const int* poles, const doub
 
 // ---------------------------------------------------------- execute tables
 
+// FP64 value -> TF32 hi + TF32 lo (both nearest)
+__device__ __forceinline__ void split_tf32(double w, float* hi, float* lo) {
+    float h = ptx::tf32_round((float)w);
+    *hi = h;
+    *lo = ptx::tf32_round((float)(w - (double)h));
+}
+
 // W[r][k] = -a_r z_k / (mu_r - lambda_k) for root rows, e_pole for deflated rows.
 __global__ void k_w_table(int n, const int* row_kind, const int* row_pole, const double* row_tau,
                           const double* row_a, const double* znd, const double* S, float* w32,
-                          double* w64) {
+                          double* w64, float* whi, float* wlo) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     int r = (int)(idx / n), k = (int)(idx % n);
@@ -206,6 +214,18 @@ __global__ void k_w_table(int n, const int* row_kind, const int* row_pole, const
     }
     if (w32) w32[idx] = (float)w;
     if (w64) w64[idx] = w;
+    if (whi) split_tf32(w, &whi[idx], &wlo[idx]);
+}
+
+// Dense X^T = W U^T (row r = eigenvector r in signal coordinates), split into
+// TF32 hi / lo: the table of the dense-GFT comparison baseline.
+__global__ void k_xt_table(int n, const double* w64, const double* ct64, float* hi, float* lo) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    int r = (int)(idx / n), j = (int)(idx % n);
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(w64[(long long)r * n + k], ct64[(long long)k * n + j], acc);
+    split_tf32(acc, &hi[idx], &lo[idx]);
 }
 
 // Ct[k][j] = c_k cos(pi k (2j+1) / 2n): the orthonormal DCT-II as a row-major matrix.
@@ -244,7 +264,8 @@ static cudaError_t dalloc(T** p, size_t count) {
 void free_plan_tables(dctplus_plan_t p) {
     void* ptrs[] = {p->d_z, p->d_sin, p->d_row_tau, p->d_row_a, p->d_row_kind, p->d_row_pole,
                     p->d_ct32, p->d_ct64, p->d_w32, p->d_w64, p->d_twiddle, p->d_gen_pole,
-                    p->d_gen_tau, p->d_gen_na, p->d_gen_z, p->d_gen_sin, p->tc.images, p->d_stage};
+                    p->d_gen_tau, p->d_gen_na, p->d_gen_z, p->d_gen_sin, p->tc.images, p->d_stage,
+                    p->d_whi, p->d_wlo, p->d_xthi, p->d_xtlo};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -371,17 +392,41 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
 
     const long long nn = (long long)n * n;
     const int blocks_nn = (int)((nn + 255) / 256);
+    // Cauchy evaluation for FP32 data with n > 64 (n <= 64 always runs the fused small-n kernels)
+    const bool gemm_shape = n > kSmallMax && n % 128 == 0 && n <= kTableMax;
+    if (n > kSmallMax) {
+        int m = p->cauchy_mode;
+        if (m == DCTPLUS_CAUCHY_AUTO) m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
+        if ((m == DCTPLUS_CAUCHY_DENSE && !gemm_shape) ||
+            (m == DCTPLUS_CAUCHY_DENSE_GFT && !(gemm_shape && n <= kF64Max)) ||
+            m == DCTPLUS_CAUCHY_HIER)
+            return DCTPLUS_ERR_UNSUPPORTED;
+        p->cauchy_mode = m;
+    }
+    const bool want_split = p->cauchy_mode == DCTPLUS_CAUCHY_DENSE;
+    const bool want_xt = p->cauchy_mode == DCTPLUS_CAUCHY_DENSE_GFT;
     if (n <= kTableMax) {
         DCTPLUS_CUDA_TRY(dalloc(&p->d_w32, nn));
         if (n <= kF64Max) DCTPLUS_CUDA_TRY(dalloc(&p->d_w64, nn));
+        if (want_split) {
+            DCTPLUS_CUDA_TRY(dalloc(&p->d_whi, nn));
+            DCTPLUS_CUDA_TRY(dalloc(&p->d_wlo, nn));
+        }
         k_w_table<<<blocks_nn, 256, 0, s>>>(n, p->d_row_kind, p->d_row_pole, p->d_row_tau,
-                                            p->d_row_a, d_znd, p->d_sin, p->d_w32, p->d_w64);
+                                            p->d_row_a, d_znd, p->d_sin, p->d_w32, p->d_w64,
+                                            p->d_whi, p->d_wlo);
         count_launch();
     }
     if (n <= kF64Max) {
         if (n <= kSmallMax) DCTPLUS_CUDA_TRY(dalloc(&p->d_ct32, nn));
         DCTPLUS_CUDA_TRY(dalloc(&p->d_ct64, nn));
         k_ct_table<<<blocks_nn, 256, 0, s>>>(n, p->d_sin, p->d_ct32, p->d_ct64);
+        count_launch();
+    }
+    if (want_xt) {
+        DCTPLUS_CUDA_TRY(dalloc(&p->d_xthi, nn));
+        DCTPLUS_CUDA_TRY(dalloc(&p->d_xtlo, nn));
+        k_xt_table<<<blocks_nn, 256, 0, s>>>(n, p->d_w64, p->d_ct64, p->d_xthi, p->d_xtlo);
         count_launch();
     }
     DCTPLUS_CUDA_TRY(dalloc(&p->d_gen_pole, n));

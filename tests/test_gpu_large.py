@@ -1,0 +1,103 @@
+"""Large-n paths against the FP64 oracle: dense split-TF32 tensor-core Cauchy
+product, the CUDA-core product, and the dense-GFT comparison baseline."""
+import numpy as np
+import pytest
+
+from oracle import cauchy
+from synthetic import edge_update_v, normal_signals, random_unit_v, self_loop_v
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_08970_gb300 as p
+    from paper_2409_08970_gb300 import build
+    build.build()
+    return p
+
+
+def relerr(y, ref):
+    return np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def run32(plan, x):
+    return plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [128, 256, 1024, 4096])
+def test_dense_tensor_core_mode_matches_oracle(pkg, n):
+    batch = 300 if n <= 1024 else 130  # ragged: not a multiple of the 128-row tile
+    for v, rho in [(random_unit_v(n), -0.3), (random_unit_v(n), 2.0), (edge_update_v(n, n // 2 - 1, n // 2), -0.5)]:
+        x = normal_signals(batch, n, seed=n)
+        ref = cauchy.transform(cauchy.make_plan(n, v, rho), x)
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_DENSE)
+        assert plan.cauchy_mode == pkg.CAUCHY_DENSE
+        err = relerr(run32(plan, x), ref)
+        assert err.max() < F32_TOL, (n, rho, err.max())
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
+
+
+def test_dense_and_cuda_core_modes_agree(pkg):
+    n, batch = 512, 257
+    v = random_unit_v(n)
+    x = normal_signals(batch, n, seed=1)
+    a = pkg.Plan(n, v, 2.0, cauchy_mode=pkg.CAUCHY_DENSE)
+    b = pkg.Plan(n, v, 2.0, cauchy_mode=pkg.CAUCHY_SIMT)
+    ya, yb = run32(a, x), run32(b, x)
+    assert relerr(ya, yb).max() < 2 * F32_TOL
+    a.close()
+    b.close()
+
+
+def test_auto_mode_picks_dense_for_gemm_shapes(pkg):
+    for n, want in [(128, pkg.CAUCHY_DENSE), (1024, pkg.CAUCHY_DENSE), (4096, pkg.CAUCHY_DENSE),
+                    (16384, pkg.CAUCHY_SIMT)]:
+        p = pkg.Plan(n, self_loop_v(n, 0), 1.0)
+        assert p.cauchy_mode == want, n
+        p.close()
+
+
+def test_unsupported_modes_are_rejected(pkg):
+    with pytest.raises(pkg.DctPlusError) as e:
+        pkg.Plan(16384, self_loop_v(16384, 0), 1.0, cauchy_mode=pkg.CAUCHY_DENSE)
+    assert e.value.status == 2
+    with pytest.raises(pkg.DctPlusError) as e:
+        pkg.Plan(2048, self_loop_v(2048, 0), 1.0, cauchy_mode=pkg.CAUCHY_DENSE_GFT)
+    assert e.value.status == 2
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_dense_gft_baseline_matches_oracle(pkg, n):
+    batch = 200
+    v = random_unit_v(n)
+    x = normal_signals(batch, n, seed=3)
+    ref = cauchy.transform(cauchy.make_plan(n, v, 2.0), x)
+    plan = pkg.Plan(n, v, 2.0, cauchy_mode=pkg.CAUCHY_DENSE_GFT)
+    err = relerr(run32(plan, x), ref)
+    assert err.max() < F32_TOL, err.max()
+    plan.close()
+
+
+def test_dense_mode_full_batch_sampled(pkg):
+    """n = 1024, batch 4096: the launch configuration the benchmark times."""
+    n, batch = 1024, 4096
+    v = random_unit_v(n)
+    x = normal_signals(batch, n, seed=0)
+    for rho in (-0.3, 2.0):
+        plan = pkg.Plan(n, v, rho)
+        y = run32(plan, x)
+        rng = np.random.default_rng(2)
+        sig = np.sort(rng.choice(batch, 128, replace=False))
+        ref = cauchy.transform(cauchy.make_plan(n, v, rho), x[sig])
+        assert relerr(y[sig], ref).max() < F32_TOL
+        pr = np.abs(np.linalg.norm(y, axis=1) / np.linalg.norm(x, axis=1) - 1)
+        assert pr.max() < 2e-6
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
