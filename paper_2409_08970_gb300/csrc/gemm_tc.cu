@@ -42,13 +42,19 @@ constexpr uint32_t kStageBytes = 4 * kSlice;          // A_hi, A_lo, B_hi, B_lo
 constexpr uint32_t kOffBar = kStages * kStageBytes;
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;
 
+constexpr int kMaxTilesN = 128;
+
+// A: [M x Ka], B: [N x K], FP32, box 32 x 128. Output tile column block tn
+// contracts B's K columns [0, K) with A's columns [kbeg[tn], kbeg[tn] + K)
+// (a band; A columns outside [0, Ka) read as zeros).
 struct Params {
-    CUtensorMap a_hi, a_lo, b_hi, b_lo;  // A: [M x K], B: [N x K], FP32, box 32 x 128
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
     float* y;
     int64_t ldy;
     int M, N, K;
     int tiles_m, tiles_n;
     unsigned* err;
+    int kbeg[kMaxTilesN];
 };
 
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ Params P) {
@@ -94,13 +100,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             int it = 0, issued = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const int m0 = (t / P.tiles_n) * kBM, n0 = (t % P.tiles_n) * kBN;
+                const int ka = P.kbeg[t % P.tiles_n];
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int s = it % kStages;
                     if (!ptx::mbar_wait(&empty[s], ((it / kStages) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
                     unsigned char* st = sm + s * kStageBytes;
                     ptx::mbar_expect_tx(&full[s], kStageBytes);
-                    ptx::tma_load_2d(st + 0 * kSlice, &P.a_hi, kc * kBK, m0, &full[s]);
-                    ptx::tma_load_2d(st + 1 * kSlice, &P.a_lo, kc * kBK, m0, &full[s]);
+                    ptx::tma_load_2d(st + 0 * kSlice, &P.a_hi, ka + kc * kBK, m0, &full[s]);
+                    ptx::tma_load_2d(st + 1 * kSlice, &P.a_lo, ka + kc * kBK, m0, &full[s]);
                     ptx::tma_load_2d(st + 2 * kSlice, &P.b_hi, kc * kBK, n0, &full[s]);
                     ptx::tma_load_2d(st + 3 * kSlice, &P.b_lo, kc * kBK, n0, &full[s]);
                     issued = it + 1;
@@ -217,13 +224,18 @@ static bool encode_rows(CUtensorMap* m, const float* base, int64_t rows, int64_t
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// y[M x N] = (a_hi + a_lo) (b_hi + b_lo)^T; K % 32 == 0, N % 128 == 0, 16-byte
-// aligned bases, leading dimensions multiples of 4 floats.
-dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda, const float* b_hi,
-                              const float* b_lo, int64_t ldb, float* y, int64_t ldy, int M, int N,
-                              int K, cudaStream_t s, int dev) {
+// y[M x N] = (a_hi + a_lo)[:, band] (b_hi + b_lo)^T. A is [M x Ka]; B is
+// [N x K]; output column tile tn uses A columns kbeg[tn] .. kbeg[tn] + K - 1
+// (nullptr kbeg: all zero, the plain product with Ka = K). K % 32 == 0,
+// N % 128 == 0, kbeg multiples of 32, 16-byte aligned bases, leading
+// dimensions multiples of 4 floats.
+dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t lda, int Ka,
+                                   const float* b_hi, const float* b_lo, int64_t ldb, float* y,
+                                   int64_t ldy, int M, int N, int K, const int* kbeg,
+                                   cudaStream_t s, int dev) {
     if (M <= 0) return DCTPLUS_OK;
-    if (K % gemm::kBK || N % gemm::kBN || (lda & 3) || (ldb & 3) || (ldy & 3))
+    if (K % gemm::kBK || N % gemm::kBN || (lda & 3) || (ldb & 3) || (ldy & 3) ||
+        N / gemm::kBN > gemm::kMaxTilesN)
         return DCTPLUS_ERR_UNSUPPORTED;
     static bool attr[64] = {};
     if (!attr[dev & 63]) {
@@ -233,7 +245,7 @@ dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda,
     }
     gemm::Params P;
     memset(&P, 0, sizeof(P));
-    if (!encode_rows(&P.a_hi, a_hi, M, K, lda) || !encode_rows(&P.a_lo, a_lo, M, K, lda) ||
+    if (!encode_rows(&P.a_hi, a_hi, M, Ka, lda) || !encode_rows(&P.a_lo, a_lo, M, Ka, lda) ||
         !encode_rows(&P.b_hi, b_hi, N, K, ldb) || !encode_rows(&P.b_lo, b_lo, N, K, ldb))
         return DCTPLUS_ERR_CUDA;
     P.y = y;
@@ -243,6 +255,10 @@ dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda,
     P.K = K;
     P.tiles_m = (M + gemm::kBM - 1) / gemm::kBM;
     P.tiles_n = N / gemm::kBN;
+    for (int t = 0; t < P.tiles_n; ++t) {
+        P.kbeg[t] = kbeg ? kbeg[t] : 0;
+        if (P.kbeg[t] % gemm::kBK) return DCTPLUS_ERR_UNSUPPORTED;
+    }
     P.err = device_error_word(dev);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -251,6 +267,16 @@ dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda,
     count_launch();
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
+}
+
+}  // namespace dctplus
+
+namespace dctplus {
+
+dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda, const float* b_hi,
+                              const float* b_lo, int64_t ldb, float* y, int64_t ldy, int M, int N,
+                              int K, cudaStream_t s, int dev) {
+    return launch_gemm_tc_band(a_hi, a_lo, lda, K, b_hi, b_lo, ldb, y, ldy, M, N, K, nullptr, s, dev);
 }
 
 }  // namespace dctplus

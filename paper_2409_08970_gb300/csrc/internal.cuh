@@ -121,6 +121,14 @@ dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream
 dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o);
 void free_plan_tables(dctplus_plan_t p);
 
+// hier.cu
+constexpr int kHierAutoMin = 2048;  // AUTO picks the hierarchical product from this n on
+bool hier_shape(int n);
+dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd);
+void free_hier(HierTables* h);
+dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
+                           int64_t batch, cudaStream_t st);
+
 // small_simt.cu
 dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
                                      int64_t ldy, int64_t batch, cudaStream_t s);

@@ -340,6 +340,7 @@ dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, f
                               st, p->device);
     }
     if (n & (n - 1)) return DCTPLUS_ERR_UNSUPPORTED;
+    if (p->cauchy_mode == DCTPLUS_CAUCHY_HIER && y_ok) return launch_hier(p, x, ldx, y, ldy, batch, st);
     if (p->cauchy_mode == DCTPLUS_CAUCHY_DENSE && p->d_whi && y_ok) {
         // Algorithm 1 steps 1-2 (DCT-II, split for the tensor cores), then y = W s
         float* ws = static_cast<float*>(plan_workspace(p, st, 2 * sizeof(float) * plane));

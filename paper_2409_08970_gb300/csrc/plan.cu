@@ -268,6 +268,8 @@ void free_plan_tables(dctplus_plan_t p) {
                     p->d_whi, p->d_wlo, p->d_xthi, p->d_xtlo};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    free_hier(p->hier);
+    p->hier = nullptr;
 }
 
 dctplus_status setup_small_tc(dctplus_plan_t p);   // small_tc.cu
@@ -396,10 +398,13 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
     const bool gemm_shape = n > kSmallMax && n % 128 == 0 && n <= kTableMax;
     if (n > kSmallMax) {
         int m = p->cauchy_mode;
-        if (m == DCTPLUS_CAUCHY_AUTO) m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
+        if (m == DCTPLUS_CAUCHY_AUTO) {
+            if (hier_shape(n) && n >= kHierAutoMin) m = DCTPLUS_CAUCHY_HIER;
+            else m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
+        }
         if ((m == DCTPLUS_CAUCHY_DENSE && !gemm_shape) ||
             (m == DCTPLUS_CAUCHY_DENSE_GFT && !(gemm_shape && n <= kF64Max)) ||
-            m == DCTPLUS_CAUCHY_HIER)
+            (m == DCTPLUS_CAUCHY_HIER && !hier_shape(n)))
             return DCTPLUS_ERR_UNSUPPORTED;
         p->cauchy_mode = m;
     }
@@ -441,6 +446,10 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
     count_launch();
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     DCTPLUS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (p->cauchy_mode == DCTPLUS_CAUCHY_HIER && n > kSmallMax) {
+        dctplus_status hs = setup_hier(p, d_znd);
+        if (hs != DCTPLUS_OK) { cudaFree(d_znd); return hs; }
+    }
     cudaFree(d_znd);
 
     dctplus_status st = DCTPLUS_OK;

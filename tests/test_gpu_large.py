@@ -56,9 +56,9 @@ def test_dense_and_cuda_core_modes_agree(pkg):
     b.close()
 
 
-def test_auto_mode_picks_dense_for_gemm_shapes(pkg):
-    for n, want in [(128, pkg.CAUCHY_DENSE), (1024, pkg.CAUCHY_DENSE), (4096, pkg.CAUCHY_DENSE),
-                    (16384, pkg.CAUCHY_SIMT)]:
+def test_auto_mode_choice(pkg):
+    for n, want in [(128, pkg.CAUCHY_DENSE), (1024, pkg.CAUCHY_DENSE), (4096, pkg.CAUCHY_HIER),
+                    (16384, pkg.CAUCHY_HIER)]:
         p = pkg.Plan(n, self_loop_v(n, 0), 1.0)
         assert p.cauchy_mode == want, n
         p.close()
@@ -83,6 +83,41 @@ def test_dense_gft_baseline_matches_oracle(pkg, n):
     err = relerr(run32(plan, x), ref)
     assert err.max() < F32_TOL, err.max()
     plan.close()
+
+
+@pytest.mark.parametrize("n", [256, 512, 1024, 4096])
+def test_hierarchical_mode_matches_oracle(pkg, n):
+    batch = 150
+    cases = [(random_unit_v(n), -0.3), (random_unit_v(n), 2.0), (self_loop_v(n, 0), 1.0),
+             (edge_update_v(n, n // 2 - 1, n // 2), -0.5), (edge_update_v(n, 5, 6), 3.0)]
+    for v, rho in cases:
+        x = normal_signals(batch, n, seed=n + 1)
+        ref = cauchy.transform(cauchy.make_plan(n, v, rho), x)
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_HIER)
+        assert plan.cauchy_mode == pkg.CAUCHY_HIER
+        err = relerr(run32(plan, x), ref)
+        assert err.max() < F32_TOL, (n, rho, err.max())
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
+
+
+def test_hierarchical_n16384_sampled(pkg):
+    n, batch = 16384, 512
+    v = random_unit_v(n)
+    x = normal_signals(batch, n, seed=0)
+    for rho in (-0.3, 2.0):
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_HIER)
+        y = run32(plan, x)
+        rng = np.random.default_rng(7)
+        rows = np.unique(np.concatenate([rng.choice(n, 40, replace=False), [0, 1, n - 2, n - 1]]))
+        sig = np.sort(rng.choice(batch, 8, replace=False))
+        ref = cauchy.transform(cauchy.make_plan(n, v, rho, roots=rows), x[sig], rows=rows)
+        err = np.abs(y[sig][:, rows] - ref).max(axis=1) / np.linalg.norm(x[sig], axis=1)
+        assert err.max() < F32_TOL, err.max()
+        pr = np.abs(np.linalg.norm(y, axis=1) / np.linalg.norm(x, axis=1) - 1)
+        assert pr.max() < 2e-6
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
 
 
 def test_dense_mode_full_batch_sampled(pkg):
