@@ -236,7 +236,12 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extra and rank == 0:
-        extra["n1024"] = bench_n1024(pkg, torch, dev, stream, args, flush, hbm_peak)
+        D, H, G = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT
+        extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 1024, 4096, [H, D, G])
+        if not args.quick:
+            extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 256, 4096, [H, D, G])
+            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 4096, 4096, [H, D])
+            extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 16384, 512, [H])
         extra["dense_gft_cublas_fp32"] = bench_dense_gft(pkg, torch, dev, stream, args, flush, wl,
                                                          plans, seg)
     cpu = None
@@ -272,26 +277,42 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def bench_n1024(pkg, torch, dev, stream, args, flush, hbm_peak):
+MODE_NAMES = {1: "dense", 2: "hierarchical", 3: "cuda_core", 4: "dense_gft_baseline"}
+
+
+def bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, n, batch, modes):
+    """Large-n forward: batch N(0,1) signals, dense unit v (seed 1), rho in {-0.3, 2.0};
+    one step = both plans over the batch. Modes are timed one after another."""
     from synthetic import normal_signals, random_unit_v
-    n, batch = 1024, 4096
     v = random_unit_v(n)
-    plans = [pkg.Plan(n, v, rho) for rho in (-0.3, 2.0)]
     x = torch.tensor(normal_signals(batch, n, seed=0), dtype=torch.float32, device=dev)
-    ys = [torch.empty_like(x) for _ in plans]
+    ys = [torch.empty_like(x) for _ in range(2)]
     sh = stream.cuda_stream
-
-    def step():
-        for p, y in zip(plans, ys):
-            pkg.dctplus_execute(p.handle, pkg.F32, x.data_ptr(), n, y.data_ptr(), n, batch, sh)
-
-    times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
-    t_ms = float(np.mean(times))
     samples = 2 * batch * n
-    return {"workload": "n=1024, batch 4096, x~N(0,1), dense unit v (seed 1), rho in {-0.3, 2.0}",
+    out = {"workload": f"n={n}, batch {batch}, x~N(0,1), dense unit v (seed 1), rho in {{-0.3, 2.0}}"}
+    for mode in modes:
+        try:
+            plans = [pkg.Plan(n, v, rho, cauchy_mode=mode) for rho in (-0.3, 2.0)]
+        except pkg.DctPlusError:
+            continue
+
+        def step():
+            for p, y in zip(plans, ys):
+                pkg.dctplus_execute(p.handle, pkg.F32, x.data_ptr(), n, y.data_ptr(), n, batch, sh)
+
+        lc = pkg.dctplus_launch_count()
+        step()
+        torch.cuda.synchronize()
+        launches = pkg.dctplus_launch_count() - lc
+        times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
+        t_ms = float(np.mean(times))
+        out[MODE_NAMES.get(plans[0].cauchy_mode, str(mode))] = {
             "value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t_ms,
-            "cauchy_mode": plans[0].cauchy_mode,
+            "launches_per_step": launches,
             "hbm_frac_of_measured": 8.0 * samples / (t_ms * 1e-3) / 1e9 / hbm_peak}
+        for p in plans:
+            p.close()
+    return out
 
 
 def bench_dense_gft(pkg, torch, dev, stream, args, flush, wl, plans, seg):
@@ -395,6 +416,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true", help="skip the n=1024 and comparator items")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--quick", action="store_true", help="only the n=1024 large-n item")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -20,7 +20,7 @@
 //               P2M at the leaves (z folded into the weights), M2M up the tree,
 //               M2L between well-separated boxes of each level, L2L down, L2P
 //               at the target leaves (-a folded into the weights); one CTA per
-//               signal on CUDA cores, added into y.
+//               group of up to 16 signals on CUDA cores, added into y.
 // Roots outside [0, 4] (at most the largest for rho > 0 or the smallest for
 // rho < 0; the paper's pre-processing isolates the same root) have no real
 // angle; their rows are dense dot products.
@@ -41,8 +41,11 @@ struct HierTables {
     std::vector<int> kbeg;       // per 128-row output tile: first source of the K window
     float* slab_hi = nullptr;    // n x Kw
     float* slab_lo = nullptr;
-    float* ps = nullptr;         // n x R: z_j S_a(th_j) in the leaf of source j
-    float* pt = nullptr;         // n x R: -a_r S_a(ph_r) in the leaf of row r (0: not a far target)
+    float* zf = nullptr;         // n: z_j (0 where deflated)
+    float* tq = nullptr;         // 64 x R: S_a at the 64 source positions of any leaf
+    float* pu = nullptr;         // n: position of row r in its leaf, in [-1, 1]
+    float* pna = nullptr;        // n: -a_r for far-field targets, 0 otherwise
+    float* cheb = nullptr;       // 2 x R: Chebyshev nodes and barycentric weights
     int* row_leaf = nullptr;     // n
     float* tlr = nullptr;        // 2 x R x R: parent basis at left / right child nodes
     float* m2l = nullptr;        // (2^(L+1) - 1) x 3 x R x R
@@ -104,7 +107,8 @@ __global__ void k_band_slab(int n, int Kw, const int* kbeg_tile, const int* row_
 
 void free_hier(HierTables* h) {
     if (!h) return;
-    void* ptrs[] = {h->slab_hi, h->slab_lo, h->ps, h->pt, h->row_leaf, h->tlr, h->m2l, h->il, h->out_w};
+    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf, h->tq, h->pu, h->pna, h->cheb,
+                    h->row_leaf, h->tlr, h->m2l, h->il, h->out_w};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
@@ -169,20 +173,24 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     }
     h->Kw = (kw + 31) / 32 * 32;
 
-    // P2M weights z_j S_a(th_j) and L2P weights -a_r S_a(ph_r)
-    std::vector<float> ps((size_t)n * kR), pt((size_t)n * kR, 0.0f);
-    for (int j = 0; j < n; ++j) {
-        int b = j / kLeaf;
-        double c = (b + 0.5) * hleaf, hw = 0.5 * hleaf;
-        double u = (M_PI * j / n - c) / hw;
-        for (int a = 0; a < kR; ++a) ps[(size_t)j * kR + a] = (float)(znd[j] * cheb_lagrange(a, u));
+    // P2M: every leaf holds 64 sources at the same relative positions, so the
+    // weights are z_j S_a(u_jj) with one 64 x R table; L2P: per-row position and -a_r
+    std::vector<float> zf(n), tq((size_t)kLeaf * kR), pu(n, 0.0f), pna(n, 0.0f), cheb(2 * kR);
+    for (int j = 0; j < n; ++j) zf[j] = (float)znd[j];
+    for (int jj = 0; jj < kLeaf; ++jj) {
+        double u = (jj + 0.0) / kLeaf * 2.0 - 1.0;  // th_j within its leaf, scaled to [-1, 1)
+        for (int a = 0; a < kR; ++a) tq[(size_t)jj * kR + a] = (float)cheb_lagrange(a, u);
     }
     for (int r = 0; r < n; ++r) {
         if (row_leaf[r] < 0 || p->row_kind[r] == 0) continue;
         int b = row_leaf[r];
         double c = (b + 0.5) * hleaf, hw = 0.5 * hleaf;
-        double u = (ph[r] - c) / hw;
-        for (int a = 0; a < kR; ++a) pt[(size_t)r * kR + a] = (float)(-p->row_a[r] * cheb_lagrange(a, u));
+        pu[r] = (float)((ph[r] - c) / hw);
+        pna[r] = (float)(-p->row_a[r]);
+    }
+    for (int a = 0; a < kR; ++a) {
+        cheb[a] = (float)cheb_node(a);
+        cheb[kR + a] = (float)(((a & 1) ? -1.0 : 1.0) * std::sin((2 * a + 1) * M_PI / (2.0 * kR)));
     }
     // transfer: parent basis at child nodes, child at (t - 1)/2 (left) or (t + 1)/2 (right)
     std::vector<float> tlr(2 * kR * kR);
@@ -233,8 +241,11 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         if (e != cudaSuccess) return e;
         return cudaMemcpy(*dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice);
     };
-    DCTPLUS_CUDA_TRY(up(&h->ps, ps));
-    DCTPLUS_CUDA_TRY(up(&h->pt, pt));
+    DCTPLUS_CUDA_TRY(up(&h->zf, zf));
+    DCTPLUS_CUDA_TRY(up(&h->tq, tq));
+    DCTPLUS_CUDA_TRY(up(&h->pu, pu));
+    DCTPLUS_CUDA_TRY(up(&h->pna, pna));
+    DCTPLUS_CUDA_TRY(up(&h->cheb, cheb));
     DCTPLUS_CUDA_TRY(up(&h->row_leaf, row_leaf));
     DCTPLUS_CUDA_TRY(up(&h->tlr, tlr));
     DCTPLUS_CUDA_TRY(up(&h->m2l, m2l));
@@ -261,8 +272,11 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
 
 struct FarArgs {
     int n, nleaf, L, nout;
-    const float* ps;
-    const float* pt;
+    const float* zf;
+    const float* tq;
+    const float* pu;
+    const float* pna;
+    const float* cheb;
     const int* row_leaf;
     const float* tlr;
     const float* m2l;
@@ -271,33 +285,50 @@ struct FarArgs {
     int out_row0, out_row1;
 };
 
-// One CTA per signal: y[b] += far-field part of W s_b (and the dense rows).
+// One CTA per group of NS signals: y[b] += far-field part of W s_b (and the
+// dense rows). Coefficient arrays are [node][a][signal], so every table value
+// read from memory serves all NS signals.
+template <int NS>
 __global__ void __launch_bounds__(256) k_far(FarArgs A, const float* __restrict__ s, int64_t lds,
                                              float* __restrict__ y, int64_t ldy, int64_t batch) {
     extern __shared__ __align__(16) float fsm[];
     const int n = A.n, nleaf = A.nleaf, L = A.L;
     const int nbox = (1 << (L + 1)) - 1;
-    float* sv = fsm;                  // n
-    float* M = sv + n;                // nbox x R multipole coefficients
-    float* Lc = M + nbox * kR;        // nbox x R local coefficients
-    float* red = Lc + nbox * kR;      // 32 scratch
+    float* sv = fsm;                      // NS x n
+    float* M = sv + NS * n;               // nbox x R x NS multipole coefficients
+    float* Lc = M + nbox * kR * NS;       // nbox x R x NS local coefficients
+    float* tq = Lc + nbox * kR * NS;      // 64 x R
+    float* tlr = tq + kLeaf * kR;         // 2 x R x R
+    float* cheb = tlr + 2 * kR * kR;      // 2 x R
+    float* red = cheb + 2 * kR;           // 8 x NS
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int64_t b = blockIdx.x; b < batch; b += gridDim.x) {
-        const float* sb = s + b * lds;
-        float* yb = y + b * ldy;
+    for (int e = tid; e < kLeaf * kR; e += nt) tq[e] = A.tq[e];
+    for (int e = tid; e < 2 * kR * kR; e += nt) tlr[e] = A.tlr[e];
+    for (int e = tid; e < 2 * kR; e += nt) cheb[e] = A.cheb[e];
+    for (int64_t b0 = (int64_t)blockIdx.x * NS; b0 < batch; b0 += (int64_t)gridDim.x * NS) {
+        const int ns = (int)min((int64_t)NS, batch - b0);
         __syncthreads();
-        for (int j = tid; j < n; j += nt) sv[j] = sb[j];
-        for (int e = tid; e < nbox * kR; e += nt) Lc[e] = 0.f;
+        for (int e = tid; e < NS * n; e += nt) {
+            int g = e / n, j = e % n;
+            sv[e] = g < ns ? s[(b0 + g) * lds + j] : 0.f;
+        }
+        for (int e = tid; e < nbox * kR * NS; e += nt) Lc[e] = 0.f;
         __syncthreads();
-        // P2M at the leaves
+        // P2M at the leaves: M[leaf][a] = sum_jj z_j S_a(u_jj) s_j
         for (int e = tid; e < nleaf * kR; e += nt) {
             int lf = e / kR, a = e % kR;
-            const float* w = A.ps + (size_t)lf * kLeaf * kR + a;
-            const float* x = sv + lf * kLeaf;
-            float acc = 0.f;
-#pragma unroll 8
-            for (int jj = 0; jj < kLeaf; ++jj) acc = fmaf(w[jj * kR], x[jj], acc);
-            M[(nleaf - 1 + lf) * kR + a] = acc;
+            float acc[NS];
+#pragma unroll
+            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+            for (int jj = 0; jj < kLeaf; ++jj) {
+                const int j = lf * kLeaf + jj;
+                const float w = A.zf[j] * tq[jj * kR + a];
+#pragma unroll
+                for (int g = 0; g < NS; ++g) acc[g] = fmaf(w, sv[g * n + j], acc[g]);
+            }
+            float* out = M + ((nleaf - 1 + lf) * kR + a) * NS;
+#pragma unroll
+            for (int g = 0; g < NS; ++g) out[g] = acc[g];
         }
         __syncthreads();
         // M2M up to level 2
@@ -305,30 +336,46 @@ __global__ void __launch_bounds__(256) k_far(FarArgs A, const float* __restrict_
             const int nb = 1 << l;
             for (int e = tid; e < nb * kR; e += nt) {
                 int bx = e / kR, a = e % kR;
-                const float* ml = M + ((2 << l) - 1 + 2 * bx) * kR;
-                const float* mr = ml + kR;
-                float acc = 0.f;
+                const float* ml = M + ((2 << l) - 1 + 2 * bx) * kR * NS;
+                const float* mr = ml + kR * NS;
+                float acc[NS];
 #pragma unroll
-                for (int a2 = 0; a2 < kR; ++a2)
-                    acc = fmaf(A.tlr[a * kR + a2], ml[a2], fmaf(A.tlr[(kR + a) * kR + a2], mr[a2], acc));
-                M[(nb - 1 + bx) * kR + a] = acc;
+                for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+#pragma unroll
+                for (int a2 = 0; a2 < kR; ++a2) {
+                    const float tl = tlr[a * kR + a2], tr = tlr[(kR + a) * kR + a2];
+#pragma unroll
+                    for (int g = 0; g < NS; ++g)
+                        acc[g] = fmaf(tl, ml[a2 * NS + g], fmaf(tr, mr[a2 * NS + g], acc[g]));
+                }
+                float* out = M + ((nb - 1 + bx) * kR + a) * NS;
+#pragma unroll
+                for (int g = 0; g < NS; ++g) out[g] = acc[g];
             }
             __syncthreads();
         }
         // M2L at every level >= 2
         for (int e = tid; e < (nbox - 3) * kR; e += nt) {
             int node = 3 + e / kR, a = e % kR;  // nodes of levels >= 2 start at index 3
-            float acc = 0.f;
+            int lvl = 31 - __clz(node + 1);
+            float acc[NS];
+#pragma unroll
+            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
             for (int q = 0; q < 3; ++q) {
                 int J = A.il[node * 3 + q];
                 if (J < 0) continue;
-                int lvl = 31 - __clz(node + 1);
-                const float* mj = M + ((1 << lvl) - 1 + J) * kR;
+                const float* mj = M + ((1 << lvl) - 1 + J) * kR * NS;
                 const float* k = A.m2l + ((size_t)(node * 3 + q) * kR + a) * kR;
 #pragma unroll
-                for (int b2 = 0; b2 < kR; ++b2) acc = fmaf(k[b2], mj[b2], acc);
+                for (int b2 = 0; b2 < kR; ++b2) {
+                    const float kv = k[b2];
+#pragma unroll
+                    for (int g = 0; g < NS; ++g) acc[g] = fmaf(kv, mj[b2 * NS + g], acc[g]);
+                }
             }
-            Lc[node * kR + a] = acc;
+            float* out = Lc + (node * kR + a) * NS;
+#pragma unroll
+            for (int g = 0; g < NS; ++g) out[g] = acc[g];
         }
         __syncthreads();
         // L2L down to the leaves
@@ -337,37 +384,77 @@ __global__ void __launch_bounds__(256) k_far(FarArgs A, const float* __restrict_
             for (int e = tid; e < 2 * nb * kR; e += nt) {
                 int c = e / kR, a2 = e % kR;  // child box at level l + 1
                 int side = c & 1;
-                const float* lp = Lc + (nb - 1 + (c >> 1)) * kR;
-                float acc = 0.f;
+                const float* lp = Lc + (nb - 1 + (c >> 1)) * kR * NS;
+                float acc[NS];
 #pragma unroll
-                for (int a = 0; a < kR; ++a) acc = fmaf(A.tlr[(side * kR + a) * kR + a2], lp[a], acc);
-                Lc[(2 * nb - 1 + c) * kR + a2] += acc;
+                for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+#pragma unroll
+                for (int a = 0; a < kR; ++a) {
+                    const float t = tlr[(side * kR + a) * kR + a2];
+#pragma unroll
+                    for (int g = 0; g < NS; ++g) acc[g] = fmaf(t, lp[a * NS + g], acc[g]);
+                }
+                float* out = Lc + ((2 * nb - 1 + c) * kR + a2) * NS;
+#pragma unroll
+                for (int g = 0; g < NS; ++g) out[g] += acc[g];
             }
             __syncthreads();
         }
-        // L2P and the update of y
+        // L2P: -a_r sum_a S_a(u_r) L[leaf][a], Lagrange weights by the barycentric formula
         for (int r = tid; r < n; r += nt) {
-            int lf = A.row_leaf[r];
-            if (lf < 0) continue;
-            const float* w = A.pt + (size_t)r * kR;
-            const float* lc = Lc + (nleaf - 1 + lf) * kR;
-            float acc = 0.f;
+            const float na = A.pna[r];
+            if (na == 0.f) continue;
+            const int lf = A.row_leaf[r];
+            const float u = A.pu[r];
+            float wts[kR], den = 0.f;
+            int hit = -1;
 #pragma unroll
-            for (int a = 0; a < kR; ++a) acc = fmaf(w[a], lc[a], acc);
-            if (acc != 0.f) yb[r] += acc;
+            for (int a = 0; a < kR; ++a) {
+                float d = u - cheb[a];
+                if (d == 0.f) hit = a;
+                wts[a] = cheb[kR + a] / d;
+                den += wts[a];
+            }
+            const float* lc = Lc + (nleaf - 1 + lf) * kR * NS;
+            float acc[NS];
+#pragma unroll
+            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+            if (hit >= 0) {
+#pragma unroll
+                for (int g = 0; g < NS; ++g) acc[g] = lc[hit * NS + g];
+            } else {
+                const float inv = 1.f / den;
+#pragma unroll
+                for (int a = 0; a < kR; ++a) {
+                    const float w = wts[a] * inv;
+#pragma unroll
+                    for (int g = 0; g < NS; ++g) acc[g] = fmaf(w, lc[a * NS + g], acc[g]);
+                }
+            }
+            for (int g = 0; g < ns; ++g) y[(b0 + g) * ldy + r] += na * acc[g];
         }
         // dense rows
         for (int o = 0; o < A.nout; ++o) {
             const float* w = A.out_w + (size_t)o * n;
-            float acc = 0.f;
-            for (int j = tid; j < n; j += nt) acc = fmaf(w[j], sv[j], acc);
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            if ((tid & 31) == 0) red[tid >> 5] = acc;
+            float acc[NS];
+#pragma unroll
+            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+            for (int j = tid; j < n; j += nt) {
+                const float wj = w[j];
+#pragma unroll
+                for (int g = 0; g < NS; ++g) acc[g] = fmaf(wj, sv[g * n + j], acc[g]);
+            }
+#pragma unroll
+            for (int g = 0; g < NS; ++g) {
+                float v = acc[g];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if ((tid & 31) == 0) red[(tid >> 5) * NS + g] = v;
+            }
             __syncthreads();
-            if (tid == 0) {
+            if (tid < ns) {
                 float t = 0.f;
-                for (int w2 = 0; w2 < nt / 32; ++w2) t += red[w2];
-                yb[o == 0 ? A.out_row0 : A.out_row1] = t;
+                for (int w2 = 0; w2 < nt / 32; ++w2) t += red[w2 * NS + tid];
+                y[(b0 + tid) * ldy + (o == 0 ? A.out_row0 : A.out_row1)] = t;
             }
             __syncthreads();
         }
@@ -399,8 +486,11 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     A.nleaf = h->nleaf;
     A.L = h->L;
     A.nout = h->nout;
-    A.ps = h->ps;
-    A.pt = h->pt;
+    A.zf = h->zf;
+    A.tq = h->tq;
+    A.pu = h->pu;
+    A.pna = h->pna;
+    A.cheb = h->cheb;
     A.row_leaf = h->row_leaf;
     A.tlr = h->tlr;
     A.m2l = h->m2l;
@@ -409,18 +499,30 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     A.out_row0 = h->out_row[0];
     A.out_row1 = h->out_row[1];
     const int nbox = (1 << (h->L + 1)) - 1;
-    size_t smem = sizeof(float) * (n + 2 * nbox * kR + 32);
-    static bool attr[64] = {};
-    if (!attr[p->device & 63]) {
-        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_far, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr[p->device & 63] = true;
+    auto smem_for = [&](int ns) {
+        return sizeof(float) * ((size_t)ns * n + 2 * (size_t)nbox * kR * ns + kLeaf * kR + 2 * kR * kR +
+                                2 * kR + 8 * ns);
+    };
+    const size_t cap = 200 * 1024;
+    int ns = 16;
+    while (ns > 1 && smem_for(ns) > cap) ns >>= 1;
+    const size_t smem = smem_for(ns);
+    int64_t groups = (batch + ns - 1) / ns;
+    int64_t grid = std::min<int64_t>(groups, (int64_t)152 * std::max(1, (int)(220 * 1024 / smem)));
+    auto launch = [&](auto kern) -> dctplus_status {
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<(unsigned)grid, 256, smem, st>>>(A, ws, n, y, ldy, batch);
+        count_launch();
+        DCTPLUS_CUDA_TRY(cudaGetLastError());
+        return DCTPLUS_OK;
+    };
+    switch (ns) {
+        case 16: return launch(k_far<16>);
+        case 8: return launch(k_far<8>);
+        case 4: return launch(k_far<4>);
+        case 2: return launch(k_far<2>);
+        default: return launch(k_far<1>);
     }
-    int per_sm = std::max(1, (int)(200 * 1024 / smem));
-    int64_t grid = std::min<int64_t>(batch, (int64_t)152 * std::min(per_sm, 8));
-    k_far<<<(unsigned)grid, 256, smem, st>>>(A, ws, n, y, ldy, batch);
-    count_launch();
-    DCTPLUS_CUDA_TRY(cudaGetLastError());
-    return DCTPLUS_OK;
 }
 
 }  // namespace dctplus

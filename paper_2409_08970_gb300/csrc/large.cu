@@ -21,22 +21,22 @@ namespace dctplus {
 
 // ------------------------------------------------------------------ tables
 
-// twiddles: [0, M/2): exp(-2 pi i j / M); [M/2, M/2 + M + 1): exp(-2 pi i k / n), k = 0..M;
-// [3M/2 + 1, 5M/2 + 2): c_k exp(-i pi k / 2n), k = 0..M
+// twiddles: [0, M): exp(-2 pi i j / M); [M, 2M + 1): exp(-2 pi i k / n), k = 0..M;
+// [2M + 1, 3M + 2): c_k exp(-i pi k / 2n), k = 0..M   (M = n / 2)
 __global__ void k_fft_tables(int n, float2* tw) {
     int M = n / 2;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < M / 2) {
+    if (idx < M) {
         double s, c;
         sincospi(-2.0 * idx / M, &s, &c);
         tw[idx] = make_float2((float)c, (float)s);
-    } else if (idx < M / 2 + M + 1) {
-        int k = idx - M / 2;
+    } else if (idx < 2 * M + 1) {
+        int k = idx - M;
         double s, c;
         sincospi(-2.0 * k / n, &s, &c);
         tw[idx] = make_float2((float)c, (float)s);
-    } else if (idx < M / 2 + 2 * (M + 1)) {
-        int k = idx - (M / 2 + M + 1);
+    } else if (idx < 3 * M + 2) {
+        int k = idx - (2 * M + 1);
         double s, c;
         sincospi(-(double)k / (2.0 * n), &s, &c);
         double ck = (k == 0) ? sqrt(1.0 / n) : sqrt(2.0 / n);
@@ -48,7 +48,7 @@ dctplus_status setup_large(dctplus_plan_t p) {
     int n = p->n;
     if (n & (n - 1)) return DCTPLUS_OK;  // FFT path only for powers of two
     int M = n / 2;
-    size_t cnt = M / 2 + 2 * (M + 1);
+    size_t cnt = 3 * M + 2;
     DCTPLUS_CUDA_TRY(cudaMalloc((void**)&p->d_twiddle, sizeof(float2) * cnt));
     k_fft_tables<<<(int)((cnt + 255) / 256), 256>>>(n, reinterpret_cast<float2*>(p->d_twiddle));
     count_launch();
@@ -67,40 +67,76 @@ __device__ __forceinline__ float tf32_lo(float v) {
     return __uint_as_float(ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu)));
 }
 
-// One CTA per signal (grid-stride over the batch). With s_lo non-null the
-// TF32 remainder of every coefficient is written there too (same layout).
+// One CTA per signal (grid-stride over the batch). The row is loaded with
+// coalesced (vector) loads into shared memory, reordered, and transformed by
+// a Stockham FFT of length M = n/2 with radix-4 stages (one radix-2 stage
+// first when log2 M is odd) and the twiddles staged in shared memory. With
+// s_lo non-null the TF32 remainder of every coefficient is written there too.
 __global__ void __launch_bounds__(512) k_dct_fft(int n, const float* __restrict__ x, int64_t ldx,
                                                  float* __restrict__ s, float* __restrict__ s_lo,
                                                  int64_t lds, int64_t batch,
-                                                 const float2* __restrict__ tw) {
+                                                 const float2* __restrict__ tw, int vec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = n / 2;
     float2* a = reinterpret_cast<float2*>(smem_raw);
     float2* b = a + M;
-    const float2* tw_fft = tw;
-    const float2* tw_split = tw + M / 2;
-    const float2* tw_post = tw + M / 2 + M + 1;
+    float2* tws = b + M;  // M twiddles exp(-2 pi i j / M)
+    const float2* tw_split = tw + M;
+    const float2* tw_post = tw + 2 * M + 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = tid; j < M; j += nt) tws[j] = tw[j];
+    int log2M = 0;
+    while ((1 << log2M) < M) ++log2M;
     for (int64_t sig = blockIdx.x; sig < batch; sig += gridDim.x) {
         const float* xs = x + sig * ldx;
+        float* xf = reinterpret_cast<float*>(b);
         __syncthreads();
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        if (vec) {
+            for (int i = tid; i < n / 4; i += nt)
+                reinterpret_cast<float4*>(xf)[i] = reinterpret_cast<const float4*>(xs)[i];
+        } else {
+            for (int i = tid; i < n; i += nt) xf[i] = xs[i];
+        }
+        __syncthreads();
+        // Makhoul reorder v_q = x_2q (q < M), x_{2n-2q-1} (q >= M); w_m = v_2m + i v_2m+1
+        for (int m = tid; m < M; m += nt) {
             int q0 = 2 * m, q1 = 2 * m + 1;
-            float v0 = q0 < M ? xs[2 * q0] : xs[2 * n - 2 * q0 - 1];
-            float v1 = q1 < M ? xs[2 * q1] : xs[2 * n - 2 * q1 - 1];
+            float v0 = q0 < M ? xf[2 * q0] : xf[2 * n - 2 * q0 - 1];
+            float v1 = q1 < M ? xf[2 * q1] : xf[2 * n - 2 * q1 - 1];
             a[m] = make_float2(v0, v1);
         }
         __syncthreads();
         float2* src = a;
         float2* dst = b;
-        for (int Ns = 1; Ns < M; Ns <<= 1) {
-            int tstep = M / (2 * Ns);
-            for (int j = threadIdx.x; j < M / 2; j += blockDim.x) {
-                int k = j & (Ns - 1);
-                float2 v0 = src[j];
-                float2 v1 = cmul(src[j + M / 2], tw_fft[k * tstep]);
-                int o = ((j - k) << 1) + k;
-                dst[o] = make_float2(v0.x + v1.x, v0.y + v1.y);
-                dst[o + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+        int Ns = 1;
+        if (log2M & 1) {  // radix-2 stage with Ns = 1 (no twiddles)
+            for (int j = tid; j < M / 2; j += nt) {
+                float2 v0 = src[j], v1 = src[j + M / 2];
+                dst[2 * j] = make_float2(v0.x + v1.x, v0.y + v1.y);
+                dst[2 * j + 1] = make_float2(v0.x - v1.x, v0.y - v1.y);
+            }
+            __syncthreads();
+            float2* t = src; src = dst; dst = t;
+            Ns = 2;
+        }
+        for (; Ns < M; Ns <<= 2) {
+            const int tstep = M / (4 * Ns);
+            for (int j = tid; j < M / 4; j += nt) {
+                const int k = j & (Ns - 1);
+                float2 v0 = src[j], v1 = src[j + M / 4], v2 = src[j + M / 2], v3 = src[j + 3 * (M / 4)];
+                if (Ns > 1) {
+                    v1 = cmul(v1, tws[k * tstep]);
+                    v2 = cmul(v2, tws[2 * k * tstep]);
+                    v3 = cmul(v3, tws[3 * k * tstep]);
+                }
+                // 4-point DFT (exp(-2 pi i / 4) = -i)
+                float2 p0 = make_float2(v0.x + v2.x, v0.y + v2.y), p1 = make_float2(v0.x - v2.x, v0.y - v2.y);
+                float2 q0 = make_float2(v1.x + v3.x, v1.y + v3.y), q1 = make_float2(v1.x - v3.x, v1.y - v3.y);
+                const int o = ((j - k) << 2) + k;
+                dst[o] = make_float2(p0.x + q0.x, p0.y + q0.y);
+                dst[o + Ns] = make_float2(p1.x + q1.y, p1.y - q1.x);
+                dst[o + 2 * Ns] = make_float2(p0.x - q0.x, p0.y - q0.y);
+                dst[o + 3 * Ns] = make_float2(p1.x - q1.y, p1.y + q1.x);
             }
             __syncthreads();
             float2* t = src; src = dst; dst = t;
@@ -137,18 +173,20 @@ dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, flo
                               float* s_lo, int64_t lds, int64_t batch, cudaStream_t st) {
     int n = p->n;
     if (!p->d_twiddle) return DCTPLUS_ERR_UNSUPPORTED;
-    size_t smem = sizeof(float2) * n;  // two buffers of n/2
+    size_t smem = sizeof(float2) * 3 * (n / 2);  // two ping-pong buffers + twiddles
     static bool attr[64] = {};
     if (!attr[p->device & 63]) {
-        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
         attr[p->device & 63] = true;
     }
-    int threads = std::min(512, std::max(32, n / 4));
-    int64_t grid = std::min<int64_t>(batch, 152 * std::max(1, (int)(200 * 1024 / std::max<size_t>(smem, 1)) ));
-    grid = std::min<int64_t>(grid, 65535 * 16);
+    int threads = std::min(512, std::max(32, n / 8));
+    int per_sm = std::max(1, std::min((int)(220 * 1024 / smem), 2048 / threads));
+    int64_t grid = std::min<int64_t>(batch, (int64_t)152 * per_sm * 2);
     if (grid <= 0) return DCTPLUS_OK;
+    const int vec = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
     k_dct_fft<<<(unsigned)grid, threads, smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch,
-                                                     reinterpret_cast<const float2*>(p->d_twiddle));
+                                                     reinterpret_cast<const float2*>(p->d_twiddle),
+                                                     vec);
     count_launch();
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
