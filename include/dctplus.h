@@ -56,7 +56,8 @@ typedef enum {
     DCTPLUS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     DCTPLUS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
     DCTPLUS_ERR_DEVICE_CHECK = 6,  /* a device-side guard recorded a violation */
-    DCTPLUS_ERR_NO_DEVICE = 7      /* no CUDA device is visible */
+    DCTPLUS_ERR_NO_DEVICE = 7,     /* no CUDA device is visible */
+    DCTPLUS_ERR_SCRATCH_LIMIT = 8  /* batch * n above the fixed scratch of dctplus_execute_noalloc */
 } dctplus_status;
 
 typedef enum { DCTPLUS_F32 = 0, DCTPLUS_F64 = 1 } dctplus_dtype;
@@ -142,6 +143,30 @@ dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const v
  * the plan (grown on demand), so calls on one plan must not overlap. */
 dctplus_status dctplus_execute_host(dctplus_plan_t plan, dctplus_dtype dtype, const void* x_host,
                                     void* y_host, int64_t batch, dctplus_stream_t stream);
+
+/* Same FP32 forward transform (Algorithm 1 steps 1-2, then Theorem 3.1's
+ * Cauchy product on the CUDA cores) for callers that cannot let the library
+ * allocate device memory while it executes. The paper has no counterpart:
+ * this is an execution variant only, with the same results as dctplus_execute
+ * up to FP32 rounding.
+ *   - Allocates nothing. The DCT-II coefficients go to a scratch array of
+ *     2^22 floats (16 MiB) compiled into the library's device image.
+ *   - Supports plans with n a power of two, 128 <= n <= 16384 (else
+ *     UNSUPPORTED), and batch * n <= 2^22 (else SCRATCH_LIMIT, before any
+ *     launch).
+ *   - x_dev, y_dev: FP32 device rows as in dctplus_execute, 4-byte aligned,
+ *     ldx, ldy >= n, not overlapping.
+ *   - The first call on a device (with the plan's device current) looks up the
+ *     scratch address; make that first call before any stream capture begins.
+ *   - The scratch need not start at zero; each call writes all it reads.
+ *   - All calls on one device share the scratch: calls that may run at the
+ *     same time (other streams or threads, unordered) race on it and must be
+ *     ordered by the caller.
+ * Asynchronous on `stream`. Errors: INVALID_ARG, UNSUPPORTED, SCRATCH_LIMIT,
+ * NO_DEVICE, CUDA. */
+dctplus_status dctplus_execute_noalloc(dctplus_plan_t plan, const float* x_dev, int64_t ldx,
+                                       float* y_dev, int64_t ldy, int64_t batch,
+                                       dctplus_stream_t stream);
 
 /* ------------------------------------------------- mixed-size batches (FP32) */
 

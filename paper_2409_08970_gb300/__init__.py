@@ -14,13 +14,14 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    CAUCHY_AUTO, CAUCHY_DENSE, CAUCHY_DENSE_GFT, CAUCHY_HIER, CAUCHY_SIMT, F32, F64, SEG_WORDS, DctPlusError, Opts,
+    CAUCHY_AUTO, CAUCHY_DENSE, CAUCHY_DENSE_GFT, CAUCHY_HIER, CAUCHY_SIMT, ERR_SCRATCH_LIMIT, F32, F64,
+    SEG_WORDS, DctPlusError, Opts,
     check,
 )
 
 __all__ = [
     "Plan", "Group", "DctPlusError", "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect",
-    "dctplus_execute", "dctplus_execute_host", "dctplus_group_create", "dctplus_group_destroy",
+    "dctplus_execute", "dctplus_execute_host", "dctplus_execute_noalloc", "dctplus_group_create", "dctplus_group_destroy",
     "dctplus_execute_group", "dctplus_execute_group_host", "dctplus_sync_check",
     "dctplus_launch_count", "dctplus_status_string", "library_path",
 ]
@@ -85,6 +86,13 @@ def dctplus_execute(handle, dtype: int, x_ptr: int, ldx: int, y_ptr: int, ldy: i
 def dctplus_execute_host(handle, dtype: int, x_ptr: int, y_ptr: int, batch: int, stream: int) -> None:
     st = _lib.load().dctplus_execute_host(handle, int(dtype), x_ptr, y_ptr, int(batch), stream)
     check(st, "dctplus_execute_host")
+
+
+def dctplus_execute_noalloc(handle, x_ptr: int, ldx: int, y_ptr: int, ldy: int, batch: int,
+                            stream: int) -> None:
+    st = _lib.load().dctplus_execute_noalloc(handle, x_ptr, int(ldx), y_ptr, int(ldy), int(batch),
+                                             stream)
+    check(st, "dctplus_execute_noalloc")
 
 
 def dctplus_group_create(handles) -> ctypes.c_void_p:

@@ -19,6 +19,7 @@ ERR_CUDA = 4
 ERR_TIMEOUT = 5
 ERR_DEVICE_CHECK = 6
 ERR_NO_DEVICE = 7
+ERR_SCRATCH_LIMIT = 8
 
 F32 = 0
 F64 = 1
@@ -35,6 +36,7 @@ SEG_WORDS = 3
 EXPORTS = (
     "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect", "dctplus_plan_size",
     "dctplus_plan_cauchy_mode", "dctplus_execute", "dctplus_execute_host",
+    "dctplus_execute_noalloc",
     "dctplus_group_create", "dctplus_group_destroy", "dctplus_execute_group",
     "dctplus_execute_group_host", "dctplus_sync_check", "dctplus_launch_count",
     "dctplus_status_string",
@@ -73,6 +75,7 @@ def load():
         "dctplus_plan_cauchy_mode": (c_int, [vp]),
         "dctplus_execute": (c_int, [vp, c_int, vp, i64, vp, i64, i64, vp]),
         "dctplus_execute_host": (c_int, [vp, c_int, vp, vp, i64, vp]),
+        "dctplus_execute_noalloc": (c_int, [vp, vp, i64, vp, i64, i64, vp]),
         "dctplus_group_create": (c_int, [ctypes.POINTER(vp), c_int, vp]),
         "dctplus_group_destroy": (None, [vp]),
         "dctplus_execute_group": (c_int, [vp, vp, vp, vp, c_int, vp]),

@@ -102,6 +102,8 @@ const char* dctplus_status_string(dctplus_status s) {
         case DCTPLUS_ERR_TIMEOUT: return "bounded device wait timed out";
         case DCTPLUS_ERR_DEVICE_CHECK: return "device-side check failed";
         case DCTPLUS_ERR_NO_DEVICE: return "no CUDA device";
+        case DCTPLUS_ERR_SCRATCH_LIMIT:
+            return "batch * n exceeds the fixed scratch of dctplus_execute_noalloc (2^22 samples)";
     }
     return "unknown status";
 }

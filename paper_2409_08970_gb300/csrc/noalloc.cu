@@ -1,0 +1,82 @@
+// dctplus_execute_noalloc: the large-n FP32 forward transform (Algorithm 1
+// steps 1-2 as the DCT-II, then the Cauchy product of Theorem 3.1 on the CUDA
+// cores) with its intermediate DCT-II coefficients held in a fixed scratch
+// array compiled into this translation unit instead of a workspace allocated
+// on demand.
+//
+// Who needs it: a caller that cannot let the library allocate device memory
+// while it executes. cudaMalloc and cudaFree may synchronise the whole device,
+// which stalls every other stream of a latency-bound serving loop, and some
+// hosts hand all device memory to their own pool up front, so an allocation
+// behind their back either fails or breaks their accounting. The ordinary
+// dctplus_execute grows a per-(plan, stream) workspace on first use, which
+// such callers cannot accept.
+//
+// Set-up: the first call on a device, with that device current, looks up the
+// device address of the scratch array (cudaGetSymbolAddress) and caches it per
+// device. That first call must come before any stream capture begins. Later
+// calls only read the cache.
+//
+// Nothing in the scratch has to start at zero: the DCT kernel writes every
+// coefficient the Cauchy kernel then reads, within the same call.
+//
+// All calls on one device share the one scratch array. Two calls whose work
+// overlaps in time (different streams, or different host threads, without an
+// ordering between them) overwrite each other's coefficients; callers must
+// order them, e.g. by issuing them on one stream.
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace dctplus {
+
+constexpr int64_t kNoAllocMaxSamples = int64_t(1) << 22;  // batch * n limit (16 MiB of FP32)
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocMaxSamples];
+
+static std::mutex g_noalloc_mu;
+static float* g_noalloc_ptr[64] = {};
+
+// Device address of the scratch array on `device` (which must be current).
+static dctplus_status noalloc_scratch(int device, float** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return DCTPLUS_ERR_CUDA;
+        g_noalloc_ptr[device] = static_cast<float*>(ptr);
+    }
+    *out = g_noalloc_ptr[device];
+    return DCTPLUS_OK;
+}
+
+}  // namespace dctplus
+
+using namespace dctplus;
+
+extern "C" dctplus_status dctplus_execute_noalloc(dctplus_plan_t p, const float* x_dev,
+                                                  int64_t ldx, float* y_dev, int64_t ldy,
+                                                  int64_t batch, dctplus_stream_t stream) {
+    if (!p || batch < 0) return DCTPLUS_ERR_INVALID_ARG;
+    if (batch == 0) return DCTPLUS_OK;
+    const int n = p->n;
+    if (!x_dev || !y_dev || ldx < n || ldy < n) return DCTPLUS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 3)
+        return DCTPLUS_ERR_INVALID_ARG;
+    const uintptr_t xa = (uintptr_t)x_dev, ya = (uintptr_t)y_dev;
+    const uintptr_t xe = xa + 4 * (size_t)((batch - 1) * ldx + n);
+    const uintptr_t ye = ya + 4 * (size_t)((batch - 1) * ldy + n);
+    if (xa < ye && ya < xe) return DCTPLUS_ERR_INVALID_ARG;
+    if (n <= kSmallMax || (n & (n - 1)) || !p->d_twiddle) return DCTPLUS_ERR_UNSUPPORTED;
+    if (batch > kNoAllocMaxSamples / n) return DCTPLUS_ERR_SCRATCH_LIMIT;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return DCTPLUS_ERR_NO_DEVICE;
+    if (cur != p->device || cur < 0 || cur >= 64) return DCTPLUS_ERR_INVALID_ARG;
+    float* s = nullptr;
+    dctplus_status st = noalloc_scratch(cur, &s);
+    if (st != DCTPLUS_OK) return st;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    st = launch_dct_fft(p, x_dev, ldx, s, nullptr, n, batch, cs);
+    if (st != DCTPLUS_OK) return st;
+    return launch_cauchy_simt(p, s, n, y_dev, ldy, batch, cs);
+}

@@ -42,7 +42,7 @@ def test_exports_via_nm(lib):
 
 
 def test_status_strings(lib):
-    for code in range(8):
+    for code in range(9):
         s = lib.dctplus_status_string(code)
         assert s and s != b"unknown status"
     assert lib.dctplus_status_string(99) == b"unknown status"
