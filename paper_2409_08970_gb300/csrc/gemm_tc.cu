@@ -14,7 +14,7 @@
 // therefore accumulated in a fresh TMEM buffer (4 large-sum roundings) and the
 // epilogue warps add the chunk into FP32 registers with round-to-nearest.
 //
-// Tiles 128 x 128, persistent CTAs (one per SM), 448 threads:
+// Tiles 128 x 128, persistent CTAs (one per SM), 320 threads:
 //   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo K-slices of 32 (3 stages)
 //   warp 1      TMEM owner (256 columns: two 128-column chunk buffers), MMA issuer
 //   warps 2..9  chunk promotion into registers, final store; two warps per
