@@ -223,3 +223,31 @@ def transform(plan: CauchyPlan, x, rows=None, block: int = 1024) -> np.ndarray:
 def transform_matrix(plan: CauchyPlan) -> np.ndarray:
     """The full n x n matrix T = X^T (rows in ascending eigenvalue order): y = T x."""
     return cauchy_rows(plan, np.arange(plan.n)) @ dct2_basis(plan.n).T
+
+
+def pruned_transform(plan: CauchyPlan, x, m_out: int, c_p: int) -> np.ndarray:
+    """Pruned coefficients of Theorem 3.4: the first m_out entries of C^ s.
+
+    W = -diag(a) C(mu, lambda) diag(z) maps the DCT coefficients s = U^T x to
+    y = W s (Theorem 3.1). C^ keeps the upper-left c_p x c_p block of W and is
+    zero elsewhere, so output i < m_out <= c_p is sum_{j < c_p} W_ij s_j. With
+    c_p = n this is exactly the first m_out coefficients of the transform.
+    """
+    n = plan.n
+    if not (1 <= m_out <= c_p <= n):
+        raise ValueError("need 1 <= m_out <= c_p <= n")
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    s = dct2(x)
+    w = cauchy_rows(plan, np.arange(m_out))
+    return s[:, :c_p] @ w[:, :c_p].T
+
+
+def pruning_bound(plan: CauchyPlan, x, c_p: int) -> np.ndarray:
+    """Right-hand side of Theorem 3.4 per signal: ||s_{c_p+1:n}|| + ||W_hl s_{1:c_p}||, with
+    W_hl the lower-left (n - c_p) x c_p block of W (the bound covers all n outputs, the
+    pruned ones being zero beyond c_p)."""
+    n = plan.n
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    s = dct2(x)
+    w_hl = cauchy_rows(plan, np.arange(c_p, n))[:, :c_p]
+    return np.linalg.norm(s[:, c_p:], axis=1) + np.linalg.norm(s[:, :c_p] @ w_hl.T, axis=1)
