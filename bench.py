@@ -136,6 +136,26 @@ def make_mixed(pkg):
     return wl, plans, seg
 
 
+def profiled_traffic():
+    """DRAM bytes (read + write) per launch of the headline kernel from its committed ncu
+    summary, or None when the kernel's sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_small_tc_mixed_2p20.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = dict(line.strip().split(": ", 1) for line in text.splitlines()
+                  if line.strip().startswith(("source_sha256: ", "traffic_bytes_per_launch: ")))
+    h = hashlib.sha256()
+    for f in ("small_tc.cu", "tc_ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2409_08970_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if fields.get("source_sha256") != h.hexdigest() or "traffic_bytes_per_launch" not in fields:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def time_graph(fn, stream, steps, warmup, flush):
     """Capture fn() in a CUDA graph; time `steps` replays with events, flushing L2 between."""
     import torch
@@ -242,6 +262,7 @@ def run_ours(args):
             extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 256, 4096, [H, D, G])
             extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 4096, 4096, [H, D])
             extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 16384, 512, [H])
+        extra["pruned_n512"] = bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak)
         extra["dense_gft_cublas_fp32"] = bench_dense_gft(pkg, torch, dev, stream, args, flush, wl,
                                                          plans, seg)
     cpu = None
@@ -258,7 +279,8 @@ def run_ours(args):
                        "segments": int(seg.shape[0]), "l2": "flushed (256 MiB write) between timed steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak, "traffic": profiled_traffic(),
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "peak_source": f"{peak_src} hbm_gbs (burst copy)",
                          "kernel": "k_small_tc" if launches_per_step == 1 else "k_small_tc + k_small_simt",
                          "kernel_ms": tk_ms, "launches_per_step": launches_per_step,
@@ -312,6 +334,48 @@ def bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, n, batch, modes)
             "hbm_frac_of_measured": 8.0 * samples / (t_ms * 1e-3) / 1e9 / hbm_peak}
         for p in plans:
             p.close()
+    return out
+
+
+def bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak, n=512, batch=16384, m_out=128):
+    """Progressive multi-transform with pruning (Theorem 3.4): one DCT-II per signal shared by
+    K = 8 self-loop updates at vertex 0 (rho = 0.25 .. 2.0), the first m_out coefficients of
+    each; exact (c_p = n) and truncated (c_p = m_out), against 8 independent full transforms."""
+    from synthetic import normal_signals, self_loop_v
+    rhos = [0.25 * (k + 1) for k in range(8)]
+    plans = [pkg.Plan(n, self_loop_v(n, 0), r) for r in rhos]
+    x = torch.tensor(normal_signals(batch, n, seed=0), dtype=torch.float32, device=dev)
+    sh = stream.cuda_stream
+    samples = batch * n
+    width = len(plans) * m_out
+    y = torch.empty(batch, width, dtype=torch.float32, device=dev)
+    ys = [torch.empty_like(x) for _ in plans]
+    out = {"workload": f"n={n}, batch {batch}, K=8 self-loop updates at vertex 0 (rho 0.25..2.0), "
+                       f"first {m_out} coefficients of each; samples = input samples"}
+
+    def timed(step, bytes_per_step):
+        lc = pkg.dctplus_launch_count()
+        step()
+        torch.cuda.synchronize()
+        launches = pkg.dctplus_launch_count() - lc
+        times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
+        t_ms = float(np.mean(times))
+        return {"value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t_ms,
+                "launches_per_step": launches,
+                "hbm_frac_of_measured": bytes_per_step / (t_ms * 1e-3) / 1e9 / hbm_peak}
+
+    handles = [p.handle for p in plans]
+    algo_bytes = 4.0 * batch * (n + width)
+    for c_p, name in ((n, "pruned_exact"), (m_out, "pruned_truncated_cp")):
+        out[name] = timed(lambda c_p=c_p: pkg.dctplus_execute_pruned(
+            handles, x.data_ptr(), n, y.data_ptr(), width, batch, m_out, c_p, sh), algo_bytes)
+
+    def full():
+        for p, yy in zip(plans, ys):
+            pkg.dctplus_execute(p.handle, pkg.F32, x.data_ptr(), n, yy.data_ptr(), n, batch, sh)
+    out["eight_full_transforms"] = timed(full, 8.0 * 8 * batch * n)
+    for p in plans:
+        p.close()
     return out
 
 

@@ -168,6 +168,35 @@ dctplus_status dctplus_execute_noalloc(dctplus_plan_t plan, const float* x_dev, 
                                        float* y_dev, int64_t ldy, int64_t batch,
                                        dctplus_stream_t stream);
 
+/* ------------------------------------------- progressive + pruned (FP32) */
+
+/* Progressive multi-transform with output pruning (Theorem 3.4, Fig. 2): K
+ * updates (v_k, rho_k) of the same path graph share one DCT-II per signal, and
+ * each keeps only its first m_out coefficients, computed from the first c_p
+ * DCT coefficients:
+ *     y_k = W_k[0:m_out, 0:c_p] s[0:c_p],  s = DCT-II(x),
+ *     W_k = -diag(a) C(mu, lambda) diag(z) of plan k (Theorem 3.1).
+ * c_p = n gives the exact first m_out coefficients of every transform;
+ * c_p < n is the truncation C^ of Theorem 3.4, whose error over all n
+ * outputs is at most ||s_{c_p+1:n}|| + ||W_hl s_{1:c_p}||.
+ *   plans  : nplans (1..64) plans, all with the same n and device (borrowed).
+ *   x_dev  : batch FP32 rows of n, leading dimension ldx >= n.
+ *   y_dev  : batch FP32 rows of nplans * m_out, leading dimension
+ *            ldy >= nplans * m_out; row b holds y_0 | y_1 | ... (plan order).
+ *   1 <= m_out <= c_p <= n. x and y must not overlap; 4-byte aligned.
+ * n > 64 must be a power of two. The tensor-core contraction runs when
+ * nplans * m_out is a multiple of 128, c_p a multiple of 32, y 16-byte aligned
+ * and ldy a multiple of 4; otherwise the CUDA-core one.
+ * The first call for a given (plans, m_out, c_p) builds and caches the stacked
+ * rows of the W_k on the device (allocates and copies synchronously, so make
+ * it before any stream capture); dctplus_destroy of any of the plans drops
+ * the cache entry. Scratch: the per-stream workspace of plans[0].
+ * Asynchronous on `stream` otherwise. Errors: INVALID_ARG, UNSUPPORTED,
+ * NO_DEVICE, CUDA. */
+dctplus_status dctplus_execute_pruned(const dctplus_plan_t* plans, int nplans, const float* x_dev,
+                                      int64_t ldx, float* y_dev, int64_t ldy, int64_t batch,
+                                      int m_out, int c_p, dctplus_stream_t stream);
+
 /* ------------------------------------------------- mixed-size batches (FP32) */
 
 /* A group of plans with n <= 64 executed together in one persistent launch:

@@ -21,7 +21,8 @@ from ._lib import (  # noqa: F401
 
 __all__ = [
     "Plan", "Group", "DctPlusError", "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect",
-    "dctplus_execute", "dctplus_execute_host", "dctplus_execute_noalloc", "dctplus_group_create", "dctplus_group_destroy",
+    "dctplus_execute", "dctplus_execute_host", "dctplus_execute_noalloc", "dctplus_execute_pruned",
+    "dctplus_group_create", "dctplus_group_destroy",
     "dctplus_execute_group", "dctplus_execute_group_host", "dctplus_sync_check",
     "dctplus_launch_count", "dctplus_status_string", "library_path",
 ]
@@ -93,6 +94,14 @@ def dctplus_execute_noalloc(handle, x_ptr: int, ldx: int, y_ptr: int, ldy: int, 
     st = _lib.load().dctplus_execute_noalloc(handle, x_ptr, int(ldx), y_ptr, int(ldy), int(batch),
                                              stream)
     check(st, "dctplus_execute_noalloc")
+
+
+def dctplus_execute_pruned(handles, x_ptr: int, ldx: int, y_ptr: int, ldy: int, batch: int,
+                           m_out: int, c_p: int, stream: int) -> None:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    st = _lib.load().dctplus_execute_pruned(arr, len(handles), x_ptr, int(ldx), y_ptr, int(ldy),
+                                            int(batch), int(m_out), int(c_p), stream)
+    check(st, "dctplus_execute_pruned")
 
 
 def dctplus_group_create(handles) -> ctypes.c_void_p:

@@ -155,6 +155,7 @@ void dctplus_destroy(dctplus_plan_t p) {
     if (cur != p->device) cudaSetDevice(p->device);
     cudaDeviceSynchronize();
     release_workspaces(p);
+    pruned_forget(p);
     free_plan_tables(p);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;

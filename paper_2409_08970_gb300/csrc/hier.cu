@@ -288,43 +288,58 @@ struct FarArgs {
 // One CTA per group of NS signals: y[b] += far-field part of W s_b (and the
 // dense rows). Coefficient arrays are [node][a][signal], so every table value
 // read from memory serves all NS signals.
+constexpr int kFarThreads = 512;
+
 template <int NS>
-__global__ void __launch_bounds__(256) k_far(FarArgs A, const float* __restrict__ s, int64_t lds,
-                                             float* __restrict__ y, int64_t ldy, int64_t batch) {
+__global__ void __launch_bounds__(kFarThreads) k_far(FarArgs A, const float* __restrict__ s, int64_t lds,
+                                                     float* __restrict__ y, int64_t ldy, int64_t batch) {
     extern __shared__ __align__(16) float fsm[];
     const int n = A.n, nleaf = A.nleaf, L = A.L;
     const int nbox = (1 << (L + 1)) - 1;
     float* sv = fsm;                      // NS x n
-    float* M = sv + NS * n;               // nbox x R x NS multipole coefficients
+    float* zf = sv + NS * n;              // n
+    float* M = zf + n;                    // nbox x R x NS multipole coefficients
     float* Lc = M + nbox * kR * NS;       // nbox x R x NS local coefficients
     float* tq = Lc + nbox * kR * NS;      // 64 x R
     float* tlr = tq + kLeaf * kR;         // 2 x R x R
     float* cheb = tlr + 2 * kR * kR;      // 2 x R
-    float* red = cheb + 2 * kR;           // 8 x NS
+    float* red = cheb + 2 * kR;           // (threads / 32) x NS
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < kLeaf * kR; e += nt) tq[e] = A.tq[e];
     for (int e = tid; e < 2 * kR * kR; e += nt) tlr[e] = A.tlr[e];
     for (int e = tid; e < 2 * kR; e += nt) cheb[e] = A.cheb[e];
+    for (int e = tid; e < n; e += nt) zf[e] = A.zf[e];
+    const int n4 = n / 4;  // n is a power of two >= 256 and lds % 4 == 0 (checked by the launcher)
     for (int64_t b0 = (int64_t)blockIdx.x * NS; b0 < batch; b0 += (int64_t)gridDim.x * NS) {
         const int ns = (int)min((int64_t)NS, batch - b0);
         __syncthreads();
-        for (int e = tid; e < NS * n; e += nt) {
-            int g = e / n, j = e % n;
-            sv[e] = g < ns ? s[(b0 + g) * lds + j] : 0.f;
+        {
+            float4* sv4 = reinterpret_cast<float4*>(sv);
+#pragma unroll 4
+            for (int e = tid; e < NS * n4; e += nt) {
+                const int g = e / n4, j4 = e - g * n4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < ns) v = __ldg(reinterpret_cast<const float4*>(s + (b0 + g) * lds) + j4);
+                sv4[e] = v;
+            }
         }
         for (int e = tid; e < nbox * kR * NS; e += nt) Lc[e] = 0.f;
         __syncthreads();
         // P2M at the leaves: M[leaf][a] = sum_jj z_j S_a(u_jj) s_j
         for (int e = tid; e < nleaf * kR; e += nt) {
-            int lf = e / kR, a = e % kR;
+            const int lf = e / kR, a = e % kR;
             float acc[NS];
 #pragma unroll
             for (int g = 0; g < NS; ++g) acc[g] = 0.f;
-            for (int jj = 0; jj < kLeaf; ++jj) {
+            for (int jj = 0; jj < kLeaf; jj += 4) {
                 const int j = lf * kLeaf + jj;
-                const float w = A.zf[j] * tq[jj * kR + a];
+                const float w0 = zf[j] * tq[jj * kR + a], w1 = zf[j + 1] * tq[(jj + 1) * kR + a];
+                const float w2 = zf[j + 2] * tq[(jj + 2) * kR + a], w3 = zf[j + 3] * tq[(jj + 3) * kR + a];
 #pragma unroll
-                for (int g = 0; g < NS; ++g) acc[g] = fmaf(w, sv[g * n + j], acc[g]);
+                for (int g = 0; g < NS; ++g) {
+                    const float4 v = *reinterpret_cast<const float4*>(sv + g * n + j);
+                    acc[g] = fmaf(w0, v.x, fmaf(w1, v.y, fmaf(w2, v.z, fmaf(w3, v.w, acc[g]))));
+                }
             }
             float* out = M + ((nleaf - 1 + lf) * kR + a) * NS;
 #pragma unroll
@@ -431,7 +446,12 @@ __global__ void __launch_bounds__(256) k_far(FarArgs A, const float* __restrict_
                     for (int g = 0; g < NS; ++g) acc[g] = fmaf(w, lc[a * NS + g], acc[g]);
                 }
             }
-            for (int g = 0; g < ns; ++g) y[(b0 + g) * ldy + r] += na * acc[g];
+            float yv[NS];
+#pragma unroll
+            for (int g = 0; g < NS; ++g) yv[g] = g < ns ? y[(b0 + g) * ldy + r] : 0.f;
+#pragma unroll
+            for (int g = 0; g < NS; ++g)
+                if (g < ns) y[(b0 + g) * ldy + r] = fmaf(na, acc[g], yv[g]);
         }
         // dense rows
         for (int o = 0; o < A.nout; ++o) {
@@ -500,18 +520,21 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     A.out_row1 = h->out_row[1];
     const int nbox = (1 << (h->L + 1)) - 1;
     auto smem_for = [&](int ns) {
-        return sizeof(float) * ((size_t)ns * n + 2 * (size_t)nbox * kR * ns + kLeaf * kR + 2 * kR * kR +
-                                2 * kR + 8 * ns);
+        return sizeof(float) * ((size_t)ns * n + n + 2 * (size_t)nbox * kR * ns + kLeaf * kR +
+                                2 * kR * kR + 2 * kR + (kFarThreads / 32) * ns);
     };
     const size_t cap = 200 * 1024;
     int ns = 16;
     while (ns > 1 && smem_for(ns) > cap) ns >>= 1;
     const size_t smem = smem_for(ns);
     int64_t groups = (batch + ns - 1) / ns;
-    int64_t grid = std::min<int64_t>(groups, (int64_t)152 * std::max(1, (int)(220 * 1024 / smem)));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    const int per_sm = std::max(1, std::min((int)(220 * 1024 / smem), 2048 / kFarThreads));
+    int64_t grid = std::min<int64_t>(groups, (int64_t)std::max(sms, 1) * per_sm);
     auto launch = [&](auto kern) -> dctplus_status {
         DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)grid, 256, smem, st>>>(A, ws, n, y, ldy, batch);
+        kern<<<(unsigned)grid, kFarThreads, smem, st>>>(A, ws, n, y, ldy, batch);
         count_launch();
         DCTPLUS_CUDA_TRY(cudaGetLastError());
         return DCTPLUS_OK;

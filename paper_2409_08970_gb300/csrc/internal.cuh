@@ -129,6 +129,9 @@ void free_hier(HierTables* h);
 dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
                            int64_t batch, cudaStream_t st);
 
+// pruned.cu
+void pruned_forget(dctplus_plan_t p);  // drop cached stacked tables that use p
+
 // small_simt.cu
 dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
                                      int64_t ldy, int64_t batch, cudaStream_t s);
