@@ -12,9 +12,11 @@ Two independent evaluations of the same transform y = X^T x:
 * ``cauchy`` (O2): the factorisation of Theorem 3.1 evaluated term by term —
   DCT-II by direct cosine sums, secular roots by bisection inside the
   Lemma 4.1 brackets, normalisation, and the Cauchy sum.
+* ``gradient``: derivatives of the transform with respect to the signal, rho and
+  v (inverse transform; first-order eigenvector perturbation).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force at n <= 8, O1 against O2).
 """
-from . import cauchy, common, definition  # noqa: F401
+from . import cauchy, common, definition, gradient  # noqa: F401
 from ._native import build as build_native  # noqa: F401
