@@ -79,7 +79,7 @@ typedef enum {
 typedef struct {
     int cauchy_mode;      /* dctplus_cauchy_mode; 0 = auto */
     int max_secular_iter; /* cap on root iterations per root; 0 = 200 */
-    int hier_rank;        /* far-field expansion order; 0 = default (16) */
+    int hier_rank;        /* reserved and ignored (the far field uses degree 12) */
     int device;           /* CUDA device ordinal; -1 = current device */
 } dctplus_opts;
 
@@ -167,6 +167,34 @@ dctplus_status dctplus_execute_host(dctplus_plan_t plan, dctplus_dtype dtype, co
 dctplus_status dctplus_execute_noalloc(dctplus_plan_t plan, const float* x_dev, int64_t ldx,
                                        float* y_dev, int64_t ldy, int64_t batch,
                                        dctplus_stream_t stream);
+
+/* ---------------------------------------------------- backward (FP32) */
+
+/* Reverse-mode derivatives of the FP32 forward transform y_b = X^T x_b, given
+ * upstream gradients g_b = dLoss/dy_b:
+ *   gx_b     = X g_b = U W^T g_b: the inverse transform, undone step by step
+ *              (Sec. 3: the transposed Cauchy product, then DCT-III);
+ *   grad_rho = sum_b sum_i g_bi w_i (K (y_b * w))_i;
+ *   grad_v   = rho X sum_b (y_b * (K^T (g_b * w)) + g_b * (K (y_b * w))),
+ * with w = X^T v, K_ik = 1 / (mu_i - mu_k) (K_ii = 0): first-order
+ * perturbation of the eigenvectors of L~ + rho v v^T (Def. 2.3). The
+ * eigenvalues do not enter y, so no derivative of them is needed.
+ *   gy_dev   : batch FP32 rows of n (ldg >= n).
+ *   y_dev    : the forward output for the same signals (ldy >= n); needed only
+ *              when grad_rho or grad_v is requested, else may be NULL.
+ *   gx_dev   : NULL, or batch FP32 rows of n (ldgx >= n) receiving X g_b;
+ *              must not overlap gy or y.
+ *   grad_rho : NULL, or one device double (overwritten).
+ *   grad_v   : NULL, or n device doubles (overwritten).
+ * 2 <= n <= 4096; device pointers 4-byte aligned. The first call for a plan
+ * builds its backward tables (W^T and K, 3 x 4 n^2 bytes each; allocates and
+ * synchronises, so make it before any stream capture); later calls use the
+ * plan's per-stream workspace (6 batch n floats). Asynchronous on `stream`
+ * otherwise. Errors: INVALID_ARG, UNSUPPORTED (n > 4096), NO_DEVICE, CUDA. */
+dctplus_status dctplus_backward(dctplus_plan_t plan, const float* gy_dev, int64_t ldg,
+                                const float* y_dev, int64_t ldy, float* gx_dev, int64_t ldgx,
+                                double* grad_rho, double* grad_v, int64_t batch,
+                                dctplus_stream_t stream);
 
 /* ------------------------------------------- progressive + pruned (FP32) */
 

@@ -22,7 +22,7 @@ from ._lib import (  # noqa: F401
 __all__ = [
     "Plan", "Group", "DctPlusError", "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect",
     "dctplus_execute", "dctplus_execute_host", "dctplus_execute_noalloc", "dctplus_execute_pruned",
-    "dctplus_group_create", "dctplus_group_destroy",
+    "dctplus_backward", "dctplus_group_create", "DctPlusFunction", "dct_plus", "dctplus_group_destroy",
     "dctplus_execute_group", "dctplus_execute_group_host", "dctplus_sync_check",
     "dctplus_launch_count", "dctplus_status_string", "library_path",
 ]
@@ -104,6 +104,14 @@ def dctplus_execute_pruned(handles, x_ptr: int, ldx: int, y_ptr: int, ldy: int, 
     check(st, "dctplus_execute_pruned")
 
 
+def dctplus_backward(handle, gy_ptr: int, ldg: int, y_ptr: int, ldy: int, gx_ptr: int, ldgx: int,
+                     grad_rho_ptr: int, grad_v_ptr: int, batch: int, stream: int) -> None:
+    st = _lib.load().dctplus_backward(handle, gy_ptr, int(ldg), y_ptr or None, int(ldy), gx_ptr or None,
+                                      int(ldgx), grad_rho_ptr or None, grad_v_ptr or None, int(batch),
+                                      stream)
+    check(st, "dctplus_backward")
+
+
 def dctplus_group_create(handles) -> ctypes.c_void_p:
     arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
     g = ctypes.c_void_p()
@@ -176,6 +184,28 @@ class Plan:
                              _stream_handle(stream) if stream is not None else 0)
         return out
 
+    def backward(self, gy, y=None, want_x: bool = True, want_params: bool = False, stream=None):
+        """Reverse-mode derivatives for float32 CUDA tensors gy (and the forward output y when
+        the parameter gradients are wanted). Returns (gx or None, grad_rho or None, grad_v or None);
+        grad_rho and grad_v are float64 tensors."""
+        import torch
+        if gy.dtype != torch.float32 or gy.dim() != 2 or gy.shape[1] != self.n or gy.stride(1) != 1:
+            raise ValueError("gy must be a float32 (batch, n) tensor with unit stride along n")
+        batch = gy.shape[0]
+        gx = torch.empty_like(gy, memory_format=torch.contiguous_format) if want_x else None
+        grad_rho = grad_v = None
+        if want_params:
+            if y is None or y.shape != gy.shape or y.dtype != torch.float32 or y.stride(1) != 1:
+                raise ValueError("y must be the float32 forward output matching gy")
+            grad_rho = torch.empty((), dtype=torch.float64, device=gy.device)
+            grad_v = torch.empty(self.n, dtype=torch.float64, device=gy.device)
+        dctplus_backward(self.handle, gy.data_ptr(), gy.stride(0), y.data_ptr() if want_params else 0,
+                         y.stride(0) if want_params else self.n, gx.data_ptr() if gx is not None else 0,
+                         gx.stride(0) if gx is not None else self.n,
+                         grad_rho.data_ptr() if grad_rho is not None else 0,
+                         grad_v.data_ptr() if grad_v is not None else 0, batch, _stream_handle(stream))
+        return gx, grad_rho, grad_v
+
     def close(self) -> None:
         if getattr(self, "handle", None) is not None and self.handle.value:
             dctplus_destroy(self.handle)
@@ -222,3 +252,67 @@ class Group:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- autograd
+
+_plan_cache: dict = {}
+
+
+def _cached_plan(n: int, v_host: np.ndarray, rho: float, device: int) -> "Plan":
+    key = (n, v_host.tobytes(), float(rho), device)
+    plan = _plan_cache.get(key)
+    if plan is None:
+        if len(_plan_cache) >= 16:
+            _plan_cache.pop(next(iter(_plan_cache))).close()
+        plan = Plan(n, v_host, float(rho), device=device)
+        _plan_cache[key] = plan
+    return plan
+
+
+def _make_function():
+    import torch
+
+    class DctPlusFunction(torch.autograd.Function):
+        """y = X(v, rho)^T x on float32 CUDA signals (rows of x), differentiable in x, v and rho.
+
+        v (n,) and rho (scalar) are float64 tensors; the plan for (v, rho) is built on the GPU
+        (and cached) in the forward. The backward calls dctplus_backward."""
+
+        @staticmethod
+        def forward(ctx, x, v, rho):
+            v_host = v.detach().to("cpu", torch.float64).numpy()
+            plan = _cached_plan(x.shape[1], v_host, float(rho), x.device.index or 0)
+            y = plan.forward(x.contiguous())
+            ctx.plan = plan
+            ctx.save_for_backward(y)
+            ctx.v_dtype, ctx.v_device = v.dtype, v.device
+            ctx.rho_dtype = rho.dtype if torch.is_tensor(rho) else torch.float64
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            (y,) = ctx.saved_tensors
+            want_x = ctx.needs_input_grad[0]
+            want_p = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+            gx, g_rho, g_v = ctx.plan.backward(gy.contiguous().float(), y, want_x=want_x,
+                                               want_params=want_p)
+            gv = g_v.to(ctx.v_device, ctx.v_dtype) if (g_v is not None and ctx.needs_input_grad[1]) else None
+            gr = g_rho.to(ctx.rho_dtype) if (g_rho is not None and ctx.needs_input_grad[2]) else None
+            return gx, gv, gr
+
+    return DctPlusFunction
+
+
+def __getattr__(name):
+    if name == "DctPlusFunction":
+        fn = _make_function()
+        globals()["DctPlusFunction"] = fn
+        return fn
+    raise AttributeError(name)
+
+
+def dct_plus(x, v, rho):
+    """Differentiable Fast DCT+ forward: y = X(v, rho)^T x for float32 CUDA rows x."""
+    import paper_2409_08970_gb300 as _self
+    return _self.DctPlusFunction.apply(x, v, rho)

@@ -36,7 +36,7 @@ SEG_WORDS = 3
 EXPORTS = (
     "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect", "dctplus_plan_size",
     "dctplus_plan_cauchy_mode", "dctplus_execute", "dctplus_execute_host",
-    "dctplus_execute_noalloc", "dctplus_execute_pruned",
+    "dctplus_execute_noalloc", "dctplus_execute_pruned", "dctplus_backward",
     "dctplus_group_create", "dctplus_group_destroy", "dctplus_execute_group",
     "dctplus_execute_group_host", "dctplus_sync_check", "dctplus_launch_count",
     "dctplus_status_string",
@@ -77,6 +77,7 @@ def load():
         "dctplus_execute_host": (c_int, [vp, c_int, vp, vp, i64, vp]),
         "dctplus_execute_noalloc": (c_int, [vp, vp, i64, vp, i64, i64, vp]),
         "dctplus_execute_pruned": (c_int, [vp, c_int, vp, i64, vp, i64, i64, c_int, c_int, vp]),
+        "dctplus_backward": (c_int, [vp, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp]),
         "dctplus_group_create": (c_int, [ctypes.POINTER(vp), c_int, vp]),
         "dctplus_group_destroy": (None, [vp]),
         "dctplus_execute_group": (c_int, [vp, vp, vp, vp, c_int, vp]),

@@ -27,8 +27,10 @@ inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_
 
 unsigned* device_error_word(int device);  // lazily allocated per device
 
-// Device tables of the hierarchical Cauchy evaluation (see cauchy_hier.cu).
+// Device tables of the hierarchical Cauchy evaluation (hier.cu) and of the
+// backward pass (backward.cu).
 struct HierTables;
+struct BackwardTables;
 
 // Tables consumed by the tensor-core small-n kernel (see small_tc.cu).
 struct SmallTcTables {
@@ -76,6 +78,7 @@ struct dctplus_plan_s {
     float* d_gen_sin = nullptr;    // sin(pi m / 2n), FP32, m = 0..2n
     dctplus::SmallTcTables tc;
     dctplus::HierTables* hier = nullptr;
+    dctplus::BackwardTables* bwd = nullptr;  // built on the first dctplus_backward call
 
     // staging for dctplus_execute_host
     void* d_stage = nullptr;
@@ -131,6 +134,12 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
 
 // pruned.cu
 void pruned_forget(dctplus_plan_t p);  // drop cached stacked tables that use p
+// y[b][r] = sum_{k < Kd} a[b][k] w[r][k] for r < N on CUDA cores (any sizes)
+dctplus_status launch_rows_gemm(const float* a, int64_t lda, const float* w, int64_t ldw, float* y,
+                                int64_t ldy, int64_t batch, int N, int Kd, cudaStream_t st);
+
+// backward.cu
+void free_backward(BackwardTables* b);
 
 // small_simt.cu
 dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
@@ -141,6 +150,9 @@ dctplus_status launch_small_simt_f64(dctplus_plan_t p, const double* x, int64_t 
 // large.cu
 dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
                               float* s_lo, int64_t lds, int64_t batch, cudaStream_t st);
+// DCT-III (inverse of the orthonormal DCT-II), n a power of two in [128, 8192]
+dctplus_status launch_idct_fft(dctplus_plan_t p, const float* s, int64_t lds, float* x, int64_t ldx,
+                               int64_t batch, cudaStream_t st);
 dctplus_status launch_cauchy_simt(dctplus_plan_t p, const float* s_in, int64_t lds, float* y,
                                   int64_t ldy, int64_t batch, cudaStream_t st);
 dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,

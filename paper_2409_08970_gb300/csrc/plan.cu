@@ -270,6 +270,8 @@ void free_plan_tables(dctplus_plan_t p) {
         if (q) cudaFree(q);
     free_hier(p->hier);
     p->hier = nullptr;
+    free_backward(p->bwd);
+    p->bwd = nullptr;
 }
 
 dctplus_status setup_small_tc(dctplus_plan_t p);   // small_tc.cu

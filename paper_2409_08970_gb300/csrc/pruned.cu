@@ -124,6 +124,8 @@ dctplus_status get_set(const dctplus_plan_t* plans, int K, int m, int cp, Pruned
     return DCTPLUS_OK;
 }
 
+}  // namespace
+
 constexpr int kRB = 64;  // signals per tile
 constexpr int kRR = 64;  // output rows per tile
 constexpr int kRK = 16;
@@ -202,8 +204,6 @@ dctplus_status launch_rows_gemm(const float* a, int64_t lda, const float* w, int
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
-
-}  // namespace
 
 void pruned_forget(dctplus_plan_t p) {
     std::lock_guard<std::mutex> lk(g_pr_mu);
