@@ -263,6 +263,7 @@ def run_ours(args):
             extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 4096, 4096, [H, D])
             extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 16384, 512, [H])
         extra["pruned_n512"] = bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak)
+        extra["backward_n1024"] = bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak)
         extra["dense_gft_cublas_fp32"] = bench_dense_gft(pkg, torch, dev, stream, args, flush, wl,
                                                          plans, seg)
     cpu = None
@@ -377,6 +378,42 @@ def bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak, n=512, batch=16
     for p in plans:
         p.close()
     return out
+
+
+def bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak, n=1024, batch=8192):
+    """Differentiable transform: n = 1024, batch 8192, loss = sum of squared coefficients
+    512..1023, dense unit v (seed 1), rho = 2.0. One step = forward + backward to x, rho and v
+    (the loss gradient 2 y on the upper half is formed on the device by torch, not timed as
+    transform work but inside the step)."""
+    from synthetic import normal_signals, random_unit_v
+    plan = pkg.Plan(n, random_unit_v(n), 2.0)
+    x = torch.tensor(normal_signals(batch, n, seed=0), dtype=torch.float32, device=dev)
+    y = torch.empty_like(x)
+    g = torch.zeros_like(x)
+    gx = torch.empty_like(x)
+    g_rho = torch.empty((), dtype=torch.float64, device=dev)
+    g_v = torch.empty(n, dtype=torch.float64, device=dev)
+    sh = stream.cuda_stream
+    samples = batch * n
+
+    def step():
+        pkg.dctplus_execute(plan.handle, pkg.F32, x.data_ptr(), n, y.data_ptr(), n, batch, sh)
+        with torch.cuda.stream(stream):
+            torch.mul(y[:, n // 2:], 2.0, out=g[:, n // 2:])
+        pkg.dctplus_backward(plan.handle, g.data_ptr(), n, y.data_ptr(), n, gx.data_ptr(), n,
+                             g_rho.data_ptr(), g_v.data_ptr(), batch, sh)
+
+    lc = pkg.dctplus_launch_count()
+    step()
+    torch.cuda.synchronize()
+    launches = pkg.dctplus_launch_count() - lc
+    times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
+    t_ms = float(np.mean(times))
+    plan.close()
+    return {"workload": f"n={n}, batch {batch}, loss = sum y[:, {n // 2}:]^2, dense unit v (seed 1), "
+                        "rho = 2.0; forward + backward to x, rho, v",
+            "value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s (forward + backward)",
+            "ms_per_step": t_ms, "launches_per_step": launches}
 
 
 def bench_dense_gft(pkg, torch, dev, stream, args, flush, wl, plans, seg):
