@@ -28,7 +28,9 @@
 //   warp 1       TMEM owner and MMA issuer (one thread)
 //   warps 2..9   x_lo and S_lo into TMEM; two warps per TMEM lane quarter,
 //                32 columns each
-//   warps 10..13 Y (TMEM) staged in shared memory and stored by TMA
+//   warps 10..13 Y (TMEM) into registers and straight to global memory (a
+//                staging copy in shared memory would compete with the MMA
+//                operand reads for shared-memory bandwidth)
 //   warp 14      the < 64/n signals of each segment that do not fill a packed
 //                row, on CUDA cores from the plan's FP32 tables
 // TMEM columns: D1[3] 0..191, D2 192..255, S_lo[2] 256..383, x_lo[2] 384..511.
@@ -59,8 +61,7 @@ constexpr uint32_t kImgBytes = 16384;               // one 64x64 TF32 operand im
 constexpr uint32_t kTileBytes = kTcRows * 64 * 4;   // 32 KB
 constexpr uint32_t kOffB = 0;                       // B1 hi, B1 lo, B2 hi, B2 lo
 constexpr uint32_t kOffX = 4 * kImgBytes;           // kStages x 32 KB
-constexpr uint32_t kOffY = kOffX + kStages * kTileBytes;
-constexpr uint32_t kOffBar = kOffY + kTileBytes;
+constexpr uint32_t kOffBar = kOffX + kStages * kTileBytes;
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;  // + barriers + alignment slack
 
 // TMEM column map
@@ -73,13 +74,13 @@ struct TcSeg {
     int tail;           // signals after the last full packed row
     const float* xt;    // first tail signal
     float* yt;
+    float* y;           // first packed row of the segment's output
     const float* ct;    // n x n FP32 U^T
     const float* w;     // n x n FP32 W
 };
 
 struct TcParams {
     CUtensorMap xmap[kTcMaxSeg];
-    CUtensorMap ymap[kTcMaxSeg];
     const float* images[kTcMaxSeg];  // 4 operand images of the segment's plan (64 KB)
     TcSeg seg[kTcMaxSeg];
     int nseg;
@@ -111,19 +112,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* Bimg = sm + kOffB;
     unsigned char* xbuf = sm + kOffX;
-    unsigned char* ybuf = sm + kOffY;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
-    uint64_t* x_full = bars + 0;     // [kStages]
-    uint64_t* x_empty = bars + 4;    // [kStages]
-    uint64_t* d1_full = bars + 8;    // [3] DCT GEMM of the tile in D1[d] done
-    uint64_t* d1_free = bars + 11;   // [3] Cauchy GEMM that read D1[d] done
-    uint64_t* s_full = bars + 14;    // [2] S_lo[b] written
-    uint64_t* xlo_full = bars + 16;  // [2] x_lo[b] written
-    uint64_t* d2_full = bars + 18;   // Cauchy GEMM of the tile in D2 done
-    uint64_t* d2_empty = bars + 19;  // D2 read out
-    uint64_t* b_full = bars + 20;
-    uint64_t* drain = bars + 21;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 24);
+    uint64_t* x_full = bars + 0;                // [kStages]
+    uint64_t* x_empty = bars + kStages;         // [kStages]
+    uint64_t* d1_full = bars + 2 * kStages;     // [3] DCT GEMM of the tile in D1[d] done
+    uint64_t* d1_free = d1_full + 3;            // [3] Cauchy GEMM that read D1[d] done
+    uint64_t* s_full = d1_free + 3;             // [2] S_lo[b] written
+    uint64_t* xlo_full = s_full + 2;            // [2] x_lo[b] written
+    uint64_t* d2_full = xlo_full + 2;           // Cauchy GEMM of the tile in D2 done
+    uint64_t* d2_empty = d2_full + 1;           // D2 read out
+    uint64_t* b_full = d2_empty + 1;
+    uint64_t* drain = b_full + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    static_assert(8 * (2 * kStages + 15) <= 256, "barrier block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -334,7 +335,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         const int q = warp & 3;
         const int r = 32 * q + lane;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
-        const int gtid = threadIdx.x - 320;     // 0..127
         uint32_t u[64];
         for (int i = 0; i < count && ok; ++i) {
             const int tile = t0 + i;
@@ -349,21 +349,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(d2_empty);
-            if (gtid == 0) ptx::bulk_wait_group_read0();  // previous Y store has read the staging
-            ptx::named_bar_sync(2, 128);
+            // row r of the tile straight from registers to global memory (no shared-memory
+            // staging, which would compete with the MMA operand reads)
+            if (row0 + r < P.seg[sg].rows64) {
+                float4* dst = reinterpret_cast<float4*>(P.seg[sg].y + (int64_t)(row0 + r) * 64);
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc)
-                *reinterpret_cast<uint4*>(ybuf + sw128_off(r, cc)) =
-                    make_uint4(u[4 * cc], u[4 * cc + 1], u[4 * cc + 2], u[4 * cc + 3]);
-            ptx::fence_proxy_async_smem();
-            ptx::named_bar_sync(2, 128);
-            if (gtid == 0) {
-                ptx::tma_store_2d(&P.ymap[sg], 0, row0, ybuf);
-                ptx::tma_store_2d(&P.ymap[sg], 32, row0, ybuf + kTileBytes / 2);
-                ptx::bulk_commit_group();
+                for (int cc = 0; cc < 16; ++cc)
+                    __stcs(dst + cc, make_float4(__uint_as_float(u[4 * cc]), __uint_as_float(u[4 * cc + 1]),
+                                                 __uint_as_float(u[4 * cc + 2]), __uint_as_float(u[4 * cc + 3])));
             }
         }
-        if (gtid == 0) ptx::bulk_wait_group0();
         if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
     } else {
         // ------------------------------------------- leftover signals (warp 14)
@@ -498,7 +493,7 @@ dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream
             const int64_t rows64 = g.rows * n / 64;
             const int64_t body = rows64 * 64 / n;
             if (g.rows <= 0) continue;
-            if (rows64 > 0 && (!encode_map(&P.xmap[ns], g.x, rows64) || !encode_map(&P.ymap[ns], g.y, rows64)))
+            if (rows64 > 0 && (!encode_map(&P.xmap[ns], g.x, rows64)))
                 return DCTPLUS_ERR_CUDA;
             P.images[ns] = g.plan->tc.images;
             TcSeg& t = P.seg[ns];
@@ -508,6 +503,7 @@ dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream
             t.tail = (int)(g.rows - body);
             t.xt = g.x + body * n;
             t.yt = g.y + body * n;
+            t.y = g.y;
             t.ct = g.plan->d_ct32;
             t.w = g.plan->d_w32;
             tiles += (int)((rows64 + kTcRows - 1) / kTcRows);
