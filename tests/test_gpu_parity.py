@@ -282,3 +282,23 @@ def test_tensor_core_path_integer_residuals(pkg):
             nz = np.linalg.norm(ref, axis=1) > 0
             assert relerr(y[nz], ref[nz]).max() < F32_TOL
             plan.close()
+
+
+def test_tensor_core_path_mixed_exact_and_inexact_tiles(pkg):
+    """Tiles whose samples are all exact in TF32 skip the x_lo product; tiles, row blocks
+    and single rows with inexact samples must not. Mix them inside one launch."""
+    n = 16
+    rows = 128 * 64 // n * 6 + 37  # six full 128-row tiles of packed rows plus a ragged tail
+    x = laplace_residuals(rows * n, seed=3).astype(np.float64).reshape(rows, n)
+    per_tile = 128 * 64 // n
+    x[per_tile:2 * per_tile] += 0.1                       # tile 1: every sample inexact
+    x[3 * per_tile + 40] += 1e-3                          # tile 3: one inexact sample
+    x[4 * per_tile:5 * per_tile:7, 5] = 1.0 / 3.0         # tile 4: a sparse set of inexact samples
+    for v, rho in [(self_loop_v(n, 0), 1.0), (edge_update_v(n, n // 2 - 1, n // 2), -0.5)]:
+        ref = cauchy.transform(cauchy.make_plan(n, v, rho), x)
+        plan = pkg.Plan(n, v, rho)
+        y = run32(plan, x)
+        nz = np.linalg.norm(ref, axis=1) > 0
+        assert relerr(y[nz], ref[nz]).max() < F32_TOL
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
