@@ -95,6 +95,17 @@ __device__ __forceinline__ int find_seg(const TcParams& P, int tile) {
     return s;
 }
 
+// Segment of a non-decreasing sequence of tiles: one search, then O(1) steps
+// (each role walks its own contiguous tile range in order).
+struct SegCursor {
+    int s;
+    __device__ __forceinline__ SegCursor(const TcParams& P, int tile) : s(find_seg(P, tile)) {}
+    __device__ __forceinline__ int at(const TcParams& P, int tile) {
+        while (s + 1 < P.nseg && P.seg[s + 1].tile_start <= tile) ++s;
+        return s;
+    }
+};
+
 // byte offset of the 16-byte chunk c (0..15) of row r in a 128-row tile in the
 // 128-byte-swizzled K-major layout (K-block c / 8)
 __device__ __forceinline__ uint32_t sw128_off(int r, int c) {
@@ -167,10 +178,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             int issued = 0;
+            SegCursor cursor(P, t0);
             for (int i = 0; i < count && ok; ++i) {
                 const int tile = t0 + i, s = i % kStages;
                 if (!ptx::mbar_wait(&x_empty[s], ((i / kStages) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
-                const int sg = find_seg(P, tile);
+                const int sg = cursor.at(P, tile);
                 const int row0 = (tile - P.seg[sg].tile_start) * kTcRows;
                 ptx::mbar_expect_tx(&x_full[s], kTileBytes);
                 ptx::tma_load_2d(xbuf + s * kTileBytes, &P.xmap[sg], 0, row0, &x_full[s]);
@@ -198,10 +210,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             auto kB16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kImgBytes / 32) + (k & 3) * 2); };
             const float* cur = nullptr;
             uint32_t nb = 0, nd = 0;
+            SegCursor cursor(P, t0);
 
             // make the operand images of tile i's plan resident (drains the tensor pipe first)
             auto ensure_plan = [&](int i) -> bool {
-                const float* img = P.images[find_seg(P, t0 + i)];
+                const float* img = P.images[cursor.at(P, t0 + i)];
                 if (img == cur) return true;
                 if (cur) {
                     ptx::mma_commit(drain);
@@ -263,7 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             if (count > 0) ok = ensure_plan(0) && mma1(0);
             for (int i = 0; i < count && ok; ++i) {
                 if (i + 1 < count) {
-                    const bool same = P.images[find_seg(P, t0 + i + 1)] == cur;
+                    const bool same = P.images[cursor.at(P, t0 + i + 1)] == cur;
                     if (same) ok = mma1(i + 1) && mma2(i);
                     else ok = mma2(i) && ensure_plan(i + 1) && mma1(i + 1);
                 } else {
@@ -336,9 +349,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         const int r = 32 * q + lane;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
         uint32_t u[64];
+        SegCursor cursor(P, t0);
         for (int i = 0; i < count && ok; ++i) {
             const int tile = t0 + i;
-            const int sg = find_seg(P, tile);
+            const int sg = cursor.at(P, tile);
             const int row0 = (tile - P.seg[sg].tile_start) * kTcRows;
             if (!ptx::mbar_wait(d2_full, i & 1, kWaitLimit)) { ok = false; break; }
             ptx::tc_fence_after();
