@@ -260,7 +260,7 @@ def run_ours(args):
         extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 1024, 4096, [H, D, G])
         if not args.quick:
             extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 256, 4096, [H, D, G])
-            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 4096, 4096, [H, D])
+            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 4096, 4096, [H, D, G])
             extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 16384, 512, [H])
         extra["pruned_n512"] = bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak)
         extra["backward_n1024"] = bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak)

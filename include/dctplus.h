@@ -73,7 +73,8 @@ typedef enum {
                                  generated tile by tile in shared memory */
     DCTPLUS_CAUCHY_DENSE_GFT = 4 /* comparison baseline, not the factored method: one dense
                                     tensor-core product with the full X^T (n % 128 == 0,
-                                    n <= 1024) */
+                                    n <= 4096; X^T built in FP64 up to n = 1024, beyond that
+                                    as W U^T on the tensor cores) */
 } dctplus_cauchy_mode;
 
 typedef struct {

@@ -174,54 +174,55 @@ __global__ void k_param_prep(const float* __restrict__ y, int64_t ldy, const flo
 
 // pq rows 0..batch-1: K (y_b * w); rows batch..2 batch-1: K (g_b * w).
 // rsum_i += sum_b (-y_bi (K (g_b * w))_i + g_bi (K (y_b * w))_i), grho += sum g_bi w_i (K (y_b * w))_i
-constexpr int kRedRows = 64;
+// Each thread sums kRedRows rows in FP32 (FP64 arithmetic is slow on this part), then the
+// partial sums meet in FP64 atomics.
+constexpr int kRedRows = 16;
 __global__ void k_param_reduce(const float* __restrict__ y, int64_t ldy, const float* __restrict__ g,
                                int64_t ldg, const float* __restrict__ w, const float* __restrict__ pq,
                                int n, int64_t batch, double* __restrict__ rsum,
                                double* __restrict__ grho) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t b0 = (int64_t)blockIdx.y * kRedRows;
-    double r = 0.0, gr = 0.0;
+    double gr = 0.0;
     if (i < n) {
-        const double wi = w[i];
+        const float wi = w[i];
         const int64_t b1 = min(batch, b0 + kRedRows);
+        float r = 0.f, g32 = 0.f;
+#pragma unroll 4
         for (int64_t b = b0; b < b1; ++b) {
-            const double p = pq[b * n + i], q = pq[(batch + b) * n + i];
-            const double yv = y[b * ldy + i], gv = g[b * ldg + i];
-            r += gv * p - yv * q;
-            gr += gv * wi * p;
+            const float p = pq[b * n + i], q = pq[(batch + b) * n + i];
+            const float yv = y[b * ldy + i], gv = g[b * ldg + i];
+            r = fmaf(gv, p, fmaf(-yv, q, r));
+            g32 = fmaf(gv * wi, p, g32);
         }
-        atomicAdd(rsum + i, r);
+        atomicAdd(rsum + i, (double)r);
+        gr = g32;
     }
     for (int off = 16; off > 0; off >>= 1) gr += __shfl_xor_sync(0xffffffffu, gr, off);
     if ((threadIdx.x & 31) == 0 && gr != 0.0) atomicAdd(grho, gr);
 }
 
-// t_j = sum_i W_ij r_i (FP64, one warp per j)
-__global__ void k_wt_apply_f64(int n, const double* __restrict__ S, const int* __restrict__ kind,
-                               const int* __restrict__ pole, const double* __restrict__ tau,
-                               const double* __restrict__ a, const double* __restrict__ znd,
-                               const double* __restrict__ r, double* __restrict__ t) {
+// out_j = scale sum_i T[j][i] r_i for a table given as TF32 hi + lo (about 22 bits),
+// accumulated in FP64 (one warp per j)
+__global__ void k_table_apply(int n, const float* __restrict__ hi, const float* __restrict__ lo,
+                              const double* __restrict__ r, double scale, double* __restrict__ out,
+                              float* __restrict__ out32) {
     const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (j >= n) return;
     double acc = 0.0;
-    for (int i = lane; i < n; i += 32) acc += w_entry(i, j, n, S, kind, pole, tau, a, znd) * r[i];
+    const float* h = hi + (size_t)j * n;
+    const float* l = lo ? lo + (size_t)j * n : nullptr;
+    for (int i = lane; i < n; i += 32) acc += ((double)h[i] + (l ? (double)l[i] : 0.0)) * r[i];
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) t[j] = acc;
+    if (lane == 0) {
+        if (out) out[j] = scale * acc;
+        if (out32) out32[j] = (float)(scale * acc);
+    }
 }
 
-// out_k = scale sum_j c_j cos(pi j (2k + 1) / 2n) t_j (FP64 DCT-III, one warp per k)
-__global__ void k_dct3_f64(int n, const double* __restrict__ t, double scale, double* __restrict__ out) {
-    const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-    if (k >= n) return;
-    double acc = 0.0;
-    for (int j = lane; j < n; j += 32) {
-        const long long m = ((long long)j * (2 * k + 1)) % (4LL * n);
-        const double cj = j == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
-        acc += cj * cospi((double)m / (2.0 * n)) * t[j];
-    }
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) out[k] = scale * acc;
+__global__ void k_scale_f32_to_f64(int n, const float* __restrict__ v, double scale, double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = scale * (double)v[j];
 }
 
 bool aligned16(const void* p, int64_t ld) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld & 3) == 0; }
@@ -271,7 +272,7 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
     BackwardTables* T = p->bwd;
 
     const size_t plane = (size_t)batch * n;
-    const size_t bytes = sizeof(float) * 6 * plane + sizeof(double) * (2 * n + 2);
+    const size_t bytes = sizeof(float) * 6 * plane + sizeof(double) * (2 * n + 2) + sizeof(float) * (2 * n + 8);
     float* ws = static_cast<float*>(plan_workspace(p, st, bytes));
     if (!ws) return DCTPLUS_ERR_CUDA;
     const bool tc_shape = n % 128 == 0;
@@ -316,12 +317,21 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
     k_param_reduce<<<grid, 256, 0, st>>>(y, ldy, gy, ldg, T->w32, pq, n, batch, rsum, grho_out);
     count_launch();
     DCTPLUS_CUDA_TRY(cudaGetLastError());
-    if (grad_v) {  // rho X rsum = rho U (W^T rsum), in FP64
-        k_wt_apply_f64<<<(n + 7) / 8, 256, 0, st>>>(n, p->d_sin, p->d_row_kind, p->d_row_pole,
-                                                    p->d_row_tau, p->d_row_a, T->znd, rsum, t64);
+    if (grad_v) {  // rho X rsum = rho U (W^T rsum): W^T from its hi / lo table, FP64 sums
+        float* t32 = reinterpret_cast<float*>(grho + 2);  // n floats after the FP64 scratch
+        float* v32 = t32 + n;
+        k_table_apply<<<(n + 7) / 8, 256, 0, st>>>(n, T->wt_hi, T->wt_lo, rsum, 1.0, t64, t32);
         count_launch();
-        k_dct3_f64<<<(n + 7) / 8, 256, 0, st>>>(n, t64, p->rho, grad_v);
-        count_launch();
+        DCTPLUS_CUDA_TRY(cudaGetLastError());
+        if (fft) {  // DCT-III of the single vector in FP32, scaled by rho into FP64
+            rc = launch_idct_fft(p, t32, n, v32, n, 1, st);
+            if (rc != DCTPLUS_OK) return rc;
+            k_scale_f32_to_f64<<<(n + 255) / 256, 256, 0, st>>>(n, v32, p->rho, grad_v);
+            count_launch();
+        } else {
+            k_table_apply<<<(n + 7) / 8, 256, 0, st>>>(n, T->u32, nullptr, t64, p->rho, grad_v, nullptr);
+            count_launch();
+        }
         DCTPLUS_CUDA_TRY(cudaGetLastError());
     }
     return DCTPLUS_OK;

@@ -45,6 +45,7 @@ struct HierTables {
     float* tq = nullptr;         // 64 x R: S_a at the 64 source positions of any leaf
     float* pu = nullptr;         // n: position of row r in its leaf, in [-1, 1]
     float* pna = nullptr;        // n: -a_r for far-field targets, 0 otherwise
+    float* wl = nullptr;         // R x n: L2P weights -a_r S_a(u_r) (0 for other rows)
     float* cheb = nullptr;       // 2 x R: Chebyshev nodes and barycentric weights
     int* row_leaf = nullptr;     // n
     float* tlr = nullptr;        // 2 x R x R: parent basis at left / right child nodes
@@ -107,7 +108,7 @@ __global__ void k_band_slab(int n, int Kw, const int* kbeg_tile, const int* row_
 
 void free_hier(HierTables* h) {
     if (!h) return;
-    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf, h->tq, h->pu, h->pna, h->cheb,
+    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf, h->tq, h->pu, h->pna, h->wl, h->cheb,
                     h->row_leaf, h->tlr, h->m2l, h->il, h->out_w};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -188,6 +189,14 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         pu[r] = (float)((ph[r] - c) / hw);
         pna[r] = (float)(-p->row_a[r]);
     }
+    std::vector<float> wl((size_t)kR * n, 0.0f);
+    for (int r = 0; r < n; ++r) {
+        if (pna[r] == 0.0f) continue;
+        int b = row_leaf[r];
+        double c = (b + 0.5) * hleaf, hw = 0.5 * hleaf;
+        for (int a = 0; a < kR; ++a)
+            wl[(size_t)a * n + r] = (float)(-p->row_a[r] * cheb_lagrange(a, (ph[r] - c) / hw));
+    }
     for (int a = 0; a < kR; ++a) {
         cheb[a] = (float)cheb_node(a);
         cheb[kR + a] = (float)(((a & 1) ? -1.0 : 1.0) * std::sin((2 * a + 1) * M_PI / (2.0 * kR)));
@@ -245,6 +254,7 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     DCTPLUS_CUDA_TRY(up(&h->tq, tq));
     DCTPLUS_CUDA_TRY(up(&h->pu, pu));
     DCTPLUS_CUDA_TRY(up(&h->pna, pna));
+    DCTPLUS_CUDA_TRY(up(&h->wl, wl));
     DCTPLUS_CUDA_TRY(up(&h->cheb, cheb));
     DCTPLUS_CUDA_TRY(up(&h->row_leaf, row_leaf));
     DCTPLUS_CUDA_TRY(up(&h->tlr, tlr));
@@ -274,9 +284,8 @@ struct FarArgs {
     int n, nleaf, L, nout;
     const float* zf;
     const float* tq;
-    const float* pu;
     const float* pna;
-    const float* cheb;
+    const float* wl;
     const int* row_leaf;
     const float* tlr;
     const float* m2l;
@@ -285,14 +294,35 @@ struct FarArgs {
     int out_row0, out_row1;
 };
 
-// One CTA per group of NS signals: y[b] += far-field part of W s_b (and the
-// dense rows). Coefficient arrays are [node][a][signal], so every table value
-// read from memory serves all NS signals.
 constexpr int kFarThreads = 512;
 
+// QS consecutive signals (a quad when NS >= 4) of the NS held in shared memory
+template <int QS>
+struct Vq {
+    float v[QS];
+};
+template <int QS>
+__device__ __forceinline__ Vq<QS> ldq(const float* p) {
+    Vq<QS> r;
+    if constexpr (QS == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int g = 0; g < QS; ++g) r.v[g] = p[g];
+    }
+    return r;
+}
+
+// One CTA per group of NS signals: y[b] += far-field part of W s_b (and the
+// dense rows). Every phase splits its work into items of QS signals so that
+// all threads stay busy; coefficient arrays are [node][a][signal] so an item
+// reads its QS values with one vector load.
 template <int NS>
 __global__ void __launch_bounds__(kFarThreads) k_far(FarArgs A, const float* __restrict__ s, int64_t lds,
                                                      float* __restrict__ y, int64_t ldy, int64_t batch) {
+    constexpr int QS = NS < 4 ? NS : 4;
+    constexpr int NQ = NS / QS;
     extern __shared__ __align__(16) float fsm[];
     const int n = A.n, nleaf = A.nleaf, L = A.L;
     const int nbox = (1 << (L + 1)) - 1;
@@ -302,12 +332,10 @@ __global__ void __launch_bounds__(kFarThreads) k_far(FarArgs A, const float* __r
     float* Lc = M + nbox * kR * NS;       // nbox x R x NS local coefficients
     float* tq = Lc + nbox * kR * NS;      // 64 x R
     float* tlr = tq + kLeaf * kR;         // 2 x R x R
-    float* cheb = tlr + 2 * kR * kR;      // 2 x R
-    float* red = cheb + 2 * kR;           // (threads / 32) x NS
+    float* red = tlr + 2 * kR * kR;       // (threads / 32) x NS
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < kLeaf * kR; e += nt) tq[e] = A.tq[e];
     for (int e = tid; e < 2 * kR * kR; e += nt) tlr[e] = A.tlr[e];
-    for (int e = tid; e < 2 * kR; e += nt) cheb[e] = A.cheb[e];
     for (int e = tid; e < n; e += nt) zf[e] = A.zf[e];
     const int n4 = n / 4;  // n is a power of two >= 256 and lds % 4 == 0 (checked by the launcher)
     for (int64_t b0 = (int64_t)blockIdx.x * NS; b0 < batch; b0 += (int64_t)gridDim.x * NS) {
@@ -323,135 +351,123 @@ __global__ void __launch_bounds__(kFarThreads) k_far(FarArgs A, const float* __r
                 sv4[e] = v;
             }
         }
-        for (int e = tid; e < nbox * kR * NS; e += nt) Lc[e] = 0.f;
         __syncthreads();
         // P2M at the leaves: M[leaf][a] = sum_jj z_j S_a(u_jj) s_j
-        for (int e = tid; e < nleaf * kR; e += nt) {
-            const int lf = e / kR, a = e % kR;
-            float acc[NS];
+        for (int e = tid; e < nleaf * kR * NQ; e += nt) {
+            const int q = e % NQ, la = e / NQ, lf = la / kR, a = la % kR;
+            float acc[QS];
 #pragma unroll
-            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+            for (int g = 0; g < QS; ++g) acc[g] = 0.f;
+            const float* sq = sv + (q * QS) * n + lf * kLeaf;
             for (int jj = 0; jj < kLeaf; jj += 4) {
                 const int j = lf * kLeaf + jj;
                 const float w0 = zf[j] * tq[jj * kR + a], w1 = zf[j + 1] * tq[(jj + 1) * kR + a];
                 const float w2 = zf[j + 2] * tq[(jj + 2) * kR + a], w3 = zf[j + 3] * tq[(jj + 3) * kR + a];
 #pragma unroll
-                for (int g = 0; g < NS; ++g) {
-                    const float4 v = *reinterpret_cast<const float4*>(sv + g * n + j);
+                for (int g = 0; g < QS; ++g) {
+                    const float4 v = *reinterpret_cast<const float4*>(sq + g * n + jj);
                     acc[g] = fmaf(w0, v.x, fmaf(w1, v.y, fmaf(w2, v.z, fmaf(w3, v.w, acc[g]))));
                 }
             }
-            float* out = M + ((nleaf - 1 + lf) * kR + a) * NS;
+            float* out = M + ((nleaf - 1 + lf) * kR + a) * NS + q * QS;
 #pragma unroll
-            for (int g = 0; g < NS; ++g) out[g] = acc[g];
+            for (int g = 0; g < QS; ++g) out[g] = acc[g];
         }
         __syncthreads();
         // M2M up to level 2
         for (int l = L - 1; l >= 2; --l) {
             const int nb = 1 << l;
-            for (int e = tid; e < nb * kR; e += nt) {
-                int bx = e / kR, a = e % kR;
-                const float* ml = M + ((2 << l) - 1 + 2 * bx) * kR * NS;
+            for (int e = tid; e < nb * kR * NQ; e += nt) {
+                const int q = e % NQ, ba = e / NQ, bx = ba / kR, a = ba % kR;
+                const float* ml = M + ((2 << l) - 1 + 2 * bx) * kR * NS + q * QS;
                 const float* mr = ml + kR * NS;
-                float acc[NS];
+                float acc[QS];
 #pragma unroll
-                for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+                for (int g = 0; g < QS; ++g) acc[g] = 0.f;
 #pragma unroll
                 for (int a2 = 0; a2 < kR; ++a2) {
                     const float tl = tlr[a * kR + a2], tr = tlr[(kR + a) * kR + a2];
+                    const Vq<QS> vl = ldq<QS>(ml + a2 * NS), vr = ldq<QS>(mr + a2 * NS);
 #pragma unroll
-                    for (int g = 0; g < NS; ++g)
-                        acc[g] = fmaf(tl, ml[a2 * NS + g], fmaf(tr, mr[a2 * NS + g], acc[g]));
+                    for (int g = 0; g < QS; ++g) acc[g] = fmaf(tl, vl.v[g], fmaf(tr, vr.v[g], acc[g]));
                 }
-                float* out = M + ((nb - 1 + bx) * kR + a) * NS;
+                float* out = M + ((nb - 1 + bx) * kR + a) * NS + q * QS;
 #pragma unroll
-                for (int g = 0; g < NS; ++g) out[g] = acc[g];
+                for (int g = 0; g < QS; ++g) out[g] = acc[g];
             }
             __syncthreads();
         }
-        // M2L at every level >= 2
-        for (int e = tid; e < (nbox - 3) * kR; e += nt) {
-            int node = 3 + e / kR, a = e % kR;  // nodes of levels >= 2 start at index 3
-            int lvl = 31 - __clz(node + 1);
-            float acc[NS];
+        // M2L at every level >= 2 (nodes of levels >= 2 start at index 3)
+        for (int e = tid; e < (nbox - 3) * kR * NQ; e += nt) {
+            const int q = e % NQ, na = e / NQ, node = 3 + na / kR, a = na % kR;
+            const int lvl = 31 - __clz(node + 1);
+            float acc[QS];
 #pragma unroll
-            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
-            for (int q = 0; q < 3; ++q) {
-                int J = A.il[node * 3 + q];
+            for (int g = 0; g < QS; ++g) acc[g] = 0.f;
+            for (int q3 = 0; q3 < 3; ++q3) {
+                const int J = A.il[node * 3 + q3];
                 if (J < 0) continue;
-                const float* mj = M + ((1 << lvl) - 1 + J) * kR * NS;
-                const float* k = A.m2l + ((size_t)(node * 3 + q) * kR + a) * kR;
+                const float* mj = M + ((1 << lvl) - 1 + J) * kR * NS + q * QS;
+                const float* k = A.m2l + ((size_t)(node * 3 + q3) * kR + a) * kR;
+                float kv[kR];
+#pragma unroll
+                for (int b2 = 0; b2 < kR; ++b2) kv[b2] = __ldg(k + b2);
 #pragma unroll
                 for (int b2 = 0; b2 < kR; ++b2) {
-                    const float kv = k[b2];
+                    const Vq<QS> v = ldq<QS>(mj + b2 * NS);
 #pragma unroll
-                    for (int g = 0; g < NS; ++g) acc[g] = fmaf(kv, mj[b2 * NS + g], acc[g]);
+                    for (int g = 0; g < QS; ++g) acc[g] = fmaf(kv[b2], v.v[g], acc[g]);
                 }
             }
-            float* out = Lc + (node * kR + a) * NS;
+            float* out = Lc + (node * kR + a) * NS + q * QS;
 #pragma unroll
-            for (int g = 0; g < NS; ++g) out[g] = acc[g];
+            for (int g = 0; g < QS; ++g) out[g] = acc[g];
         }
         __syncthreads();
         // L2L down to the leaves
         for (int l = 2; l < L; ++l) {
             const int nb = 1 << l;
-            for (int e = tid; e < 2 * nb * kR; e += nt) {
-                int c = e / kR, a2 = e % kR;  // child box at level l + 1
-                int side = c & 1;
-                const float* lp = Lc + (nb - 1 + (c >> 1)) * kR * NS;
-                float acc[NS];
+            for (int e = tid; e < 2 * nb * kR * NQ; e += nt) {
+                const int q = e % NQ, ca = e / NQ, c = ca / kR, a2 = ca % kR;  // child box at level l + 1
+                const int side = c & 1;
+                const float* lp = Lc + (nb - 1 + (c >> 1)) * kR * NS + q * QS;
+                float acc[QS];
 #pragma unroll
-                for (int g = 0; g < NS; ++g) acc[g] = 0.f;
+                for (int g = 0; g < QS; ++g) acc[g] = 0.f;
 #pragma unroll
                 for (int a = 0; a < kR; ++a) {
                     const float t = tlr[(side * kR + a) * kR + a2];
+                    const Vq<QS> v = ldq<QS>(lp + a * NS);
 #pragma unroll
-                    for (int g = 0; g < NS; ++g) acc[g] = fmaf(t, lp[a * NS + g], acc[g]);
+                    for (int g = 0; g < QS; ++g) acc[g] = fmaf(t, v.v[g], acc[g]);
                 }
-                float* out = Lc + ((2 * nb - 1 + c) * kR + a2) * NS;
+                float* out = Lc + ((2 * nb - 1 + c) * kR + a2) * NS + q * QS;
 #pragma unroll
-                for (int g = 0; g < NS; ++g) out[g] += acc[g];
+                for (int g = 0; g < QS; ++g) out[g] += acc[g];
             }
             __syncthreads();
         }
-        // L2P: -a_r sum_a S_a(u_r) L[leaf][a], Lagrange weights by the barycentric formula
-        for (int r = tid; r < n; r += nt) {
-            const float na = A.pna[r];
-            if (na == 0.f) continue;
-            const int lf = A.row_leaf[r];
-            const float u = A.pu[r];
-            float wts[kR], den = 0.f;
-            int hit = -1;
+        // L2P: y_r += sum_a w[a][r] L[leaf(r)][a] with w = -a_r S_a(u_r) from the table
+        for (int e = tid; e < n * NQ; e += nt) {
+            const int q = e / n, r = e - q * n;
+            if (A.pna[r] == 0.f) continue;
+            const float* lc = Lc + (nleaf - 1 + A.row_leaf[r]) * kR * NS + q * QS;
+            float acc[QS];
+#pragma unroll
+            for (int g = 0; g < QS; ++g) acc[g] = 0.f;
 #pragma unroll
             for (int a = 0; a < kR; ++a) {
-                float d = u - cheb[a];
-                if (d == 0.f) hit = a;
-                wts[a] = cheb[kR + a] / d;
-                den += wts[a];
+                const float w = __ldg(A.wl + (size_t)a * n + r);
+                const Vq<QS> v = ldq<QS>(lc + a * NS);
+#pragma unroll
+                for (int g = 0; g < QS; ++g) acc[g] = fmaf(w, v.v[g], acc[g]);
             }
-            const float* lc = Lc + (nleaf - 1 + lf) * kR * NS;
-            float acc[NS];
+            float yv[QS];
 #pragma unroll
-            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
-            if (hit >= 0) {
+            for (int g = 0; g < QS; ++g) yv[g] = (q * QS + g < ns) ? y[(b0 + q * QS + g) * ldy + r] : 0.f;
 #pragma unroll
-                for (int g = 0; g < NS; ++g) acc[g] = lc[hit * NS + g];
-            } else {
-                const float inv = 1.f / den;
-#pragma unroll
-                for (int a = 0; a < kR; ++a) {
-                    const float w = wts[a] * inv;
-#pragma unroll
-                    for (int g = 0; g < NS; ++g) acc[g] = fmaf(w, lc[a * NS + g], acc[g]);
-                }
-            }
-            float yv[NS];
-#pragma unroll
-            for (int g = 0; g < NS; ++g) yv[g] = g < ns ? y[(b0 + g) * ldy + r] : 0.f;
-#pragma unroll
-            for (int g = 0; g < NS; ++g)
-                if (g < ns) y[(b0 + g) * ldy + r] = fmaf(na, acc[g], yv[g]);
+            for (int g = 0; g < QS; ++g)
+                if (q * QS + g < ns) y[(b0 + q * QS + g) * ldy + r] = yv[g] + acc[g];
         }
         // dense rows
         for (int o = 0; o < A.nout; ++o) {
@@ -508,9 +524,8 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     A.nout = h->nout;
     A.zf = h->zf;
     A.tq = h->tq;
-    A.pu = h->pu;
     A.pna = h->pna;
-    A.cheb = h->cheb;
+    A.wl = h->wl;
     A.row_leaf = h->row_leaf;
     A.tlr = h->tlr;
     A.m2l = h->m2l;
@@ -521,9 +536,9 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     const int nbox = (1 << (h->L + 1)) - 1;
     auto smem_for = [&](int ns) {
         return sizeof(float) * ((size_t)ns * n + n + 2 * (size_t)nbox * kR * ns + kLeaf * kR +
-                                2 * kR * kR + 2 * kR + (kFarThreads / 32) * ns);
+                                2 * kR * kR + (kFarThreads / 32) * ns);
     };
-    const size_t cap = 200 * 1024;
+    const size_t cap = 100 * 1024;  // several CTAs per SM
     int ns = 16;
     while (ns > 1 && smem_for(ns) > cap) ns >>= 1;
     const size_t smem = smem_for(ns);

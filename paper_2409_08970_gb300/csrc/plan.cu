@@ -228,6 +228,23 @@ __global__ void k_xt_table(int n, const double* w64, const double* ct64, float* 
     split_tf32(acc, &hi[idx], &lo[idx]);
 }
 
+// Rows of U (U[c][k] = c_k cos(pi k (2c + 1) / 2n)) as TF32 hi / lo: the B operand of
+// X^T = W U^T on the tensor cores (dense-GFT comparator for n > 1024).
+__global__ void k_u_rows(int n, const double* S, float* hi, float* lo) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    int c = (int)(idx / n), k = (int)(idx % n);
+    double ck = (k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n));
+    split_tf32(ck * cos_half_pi_over_n((long long)k * (2LL * c + 1), n, S), &hi[idx], &lo[idx]);
+}
+
+// FP32 table to TF32 hi / lo (both rounded)
+__global__ void k_split_table(long long count, const float* v, float* hi, float* lo) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count) return;
+    split_tf32((double)v[idx], &hi[idx], &lo[idx]);
+}
+
 // Ct[k][j] = c_k cos(pi k (2j+1) / 2n): the orthonormal DCT-II as a row-major matrix.
 __global__ void k_ct_table(int n, const double* S, float* ct32, double* ct64) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,6 +292,9 @@ void free_plan_tables(dctplus_plan_t p) {
 }
 
 dctplus_status setup_small_tc(dctplus_plan_t p);   // small_tc.cu
+dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda, const float* b_hi,
+                              const float* b_lo, int64_t ldb, float* y, int64_t ldy, int M, int N,
+                              int K, cudaStream_t s, int dev);  // gemm_tc.cu
 dctplus_status setup_large(dctplus_plan_t p);      // large.cu
 
 dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
@@ -405,13 +425,14 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
             else m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
         }
         if ((m == DCTPLUS_CAUCHY_DENSE && !gemm_shape) ||
-            (m == DCTPLUS_CAUCHY_DENSE_GFT && !(gemm_shape && n <= kF64Max)) ||
+            (m == DCTPLUS_CAUCHY_DENSE_GFT && !gemm_shape) ||
             (m == DCTPLUS_CAUCHY_HIER && !hier_shape(n)))
             return DCTPLUS_ERR_UNSUPPORTED;
         p->cauchy_mode = m;
     }
-    const bool want_split = p->cauchy_mode == DCTPLUS_CAUCHY_DENSE;
     const bool want_xt = p->cauchy_mode == DCTPLUS_CAUCHY_DENSE_GFT;
+    // W split is also the operand that builds X^T for the comparator beyond the FP64 table size
+    const bool want_split = p->cauchy_mode == DCTPLUS_CAUCHY_DENSE || (want_xt && n > kF64Max);
     if (n <= kTableMax) {
         DCTPLUS_CUDA_TRY(dalloc(&p->d_w32, nn));
         if (n <= kF64Max) DCTPLUS_CUDA_TRY(dalloc(&p->d_w64, nn));
@@ -433,8 +454,34 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
     if (want_xt) {
         DCTPLUS_CUDA_TRY(dalloc(&p->d_xthi, nn));
         DCTPLUS_CUDA_TRY(dalloc(&p->d_xtlo, nn));
-        k_xt_table<<<blocks_nn, 256, 0, s>>>(n, p->d_w64, p->d_ct64, p->d_xthi, p->d_xtlo);
-        count_launch();
+        if (n <= kF64Max) {
+            k_xt_table<<<blocks_nn, 256, 0, s>>>(n, p->d_w64, p->d_ct64, p->d_xthi, p->d_xtlo);
+            count_launch();
+        } else {
+            // X^T = W U^T with the split-TF32 tensor-core GEMM (FP32 accurate), then split
+            float *uhi = nullptr, *ulo = nullptr, *xt = nullptr;
+            dctplus_status st = DCTPLUS_OK;
+            if (dalloc(&uhi, nn) != cudaSuccess || dalloc(&ulo, nn) != cudaSuccess ||
+                dalloc(&xt, nn) != cudaSuccess) {
+                st = DCTPLUS_ERR_CUDA;
+            } else {
+                k_u_rows<<<blocks_nn, 256, 0, s>>>(n, p->d_sin, uhi, ulo);
+                count_launch();
+                st = launch_gemm_tc(p->d_whi, p->d_wlo, n, uhi, ulo, n, xt, n, n, n, n, s, p->device);
+                if (st == DCTPLUS_OK) {
+                    k_split_table<<<blocks_nn, 256, 0, s>>>(nn, xt, p->d_xthi, p->d_xtlo);
+                    count_launch();
+                    if (cudaStreamSynchronize(s) != cudaSuccess) st = DCTPLUS_ERR_CUDA;
+                }
+            }
+            cudaFree(uhi);
+            cudaFree(ulo);
+            cudaFree(xt);
+            cudaFree(p->d_whi);
+            cudaFree(p->d_wlo);
+            p->d_whi = p->d_wlo = nullptr;
+            if (st != DCTPLUS_OK) return st;
+        }
     }
     DCTPLUS_CUDA_TRY(dalloc(&p->d_gen_pole, n));
     DCTPLUS_CUDA_TRY(dalloc(&p->d_gen_tau, n));

@@ -69,13 +69,13 @@ def test_unsupported_modes_are_rejected(pkg):
         pkg.Plan(16384, self_loop_v(16384, 0), 1.0, cauchy_mode=pkg.CAUCHY_DENSE)
     assert e.value.status == 2
     with pytest.raises(pkg.DctPlusError) as e:
-        pkg.Plan(2048, self_loop_v(2048, 0), 1.0, cauchy_mode=pkg.CAUCHY_DENSE_GFT)
+        pkg.Plan(8192, self_loop_v(8192, 0), 1.0, cauchy_mode=pkg.CAUCHY_DENSE_GFT)
     assert e.value.status == 2
 
 
-@pytest.mark.parametrize("n", [256, 1024])
+@pytest.mark.parametrize("n", [256, 1024, 2048, 4096])
 def test_dense_gft_baseline_matches_oracle(pkg, n):
-    batch = 200
+    batch = 200 if n <= 1024 else 40
     v = random_unit_v(n)
     x = normal_signals(batch, n, seed=3)
     ref = cauchy.transform(cauchy.make_plan(n, v, 2.0), x)
