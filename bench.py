@@ -234,7 +234,7 @@ def run_ours(args):
     # end to end through the host-buffer C entry point (pinned host memory)
     xh = torch.empty(x.numel(), dtype=torch.float32, pin_memory=True)
     xh.copy_(torch.from_numpy(wl.x))
-    yh = torch.empty_like(xh)
+    yh = torch.empty(x.numel(), dtype=torch.float32, pin_memory=True)
     xh_np, yh_np = xh.numpy(), yh.numpy()
 
     def e2e_step():

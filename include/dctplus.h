@@ -250,7 +250,12 @@ dctplus_status dctplus_execute_group(dctplus_group_t group, const float* x_dev, 
                                      const int64_t* seg_host, int nseg, dctplus_stream_t stream);
 
 /* Host-buffer variant of dctplus_execute_group (copies inside, synchronous).
- * total_elems = size of x_host and y_host in floats. */
+ * total_elems = size of x_host and y_host in floats. For large batches of
+ * tensor-core segments (>= 2^22 samples) the work runs in chunks so that the
+ * upload of one chunk, the kernel of the previous and the download of the one
+ * before overlap (the group's own streams plus `stream`); only the address
+ * ranges of the segments are copied back. Pinned host memory is needed for
+ * the copies to overlap. */
 dctplus_status dctplus_execute_group_host(dctplus_group_t group, const float* x_host,
                                           float* y_host, int64_t total_elems,
                                           const int64_t* seg_host, int nseg,

@@ -86,6 +86,94 @@ static dctplus_status check_device(int want) {
     return cur == want ? DCTPLUS_OK : DCTPLUS_ERR_INVALID_ARG;
 }
 
+// Host-buffer execution in chunks so that the host-to-device copy of chunk c + 1,
+// the kernel of chunk c and the device-to-host copy of chunk c - 1 overlap (three
+// streams: the caller's for uploads, two of the group's for kernels and downloads).
+// Segments are cut at whole 128-row tiles of packed rows (8192 samples), so every
+// piece is a valid tensor-core segment; each chunk copies the address range its
+// pieces cover, merged where pieces touch.
+constexpr int64_t kPipeMinElems = int64_t(1) << 22;  // below this one pass is as fast
+constexpr int kPipeChunks = 8;
+constexpr int64_t kPipeCut = 128 * 64;                // samples per tensor-core tile
+
+static dctplus_status group_host_pipelined(dctplus_group_t g, const float* x_host, float* y_host,
+                                           float* dx, float* dy, const int64_t* seg, int nseg,
+                                           cudaStream_t up) {
+    if (!g->pipe_compute) {
+        DCTPLUS_CUDA_TRY(cudaStreamCreateWithFlags(&g->pipe_compute, cudaStreamNonBlocking));
+        DCTPLUS_CUDA_TRY(cudaStreamCreateWithFlags(&g->pipe_d2h, cudaStreamNonBlocking));
+        for (int i = 0; i < 2 * kPipeChunks + 1; ++i) {
+            cudaEvent_t e;
+            DCTPLUS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            g->pipe_events.push_back(e);
+        }
+    }
+    // pieces: (plan, offset, rows), in the callers' segment order
+    struct Piece { dctplus_plan_t p; int64_t off, rows, elems; };
+    std::vector<Piece> pieces;
+    int64_t total = 0;
+    for (int i = 0; i < nseg; ++i) {
+        const int64_t rows = seg[3 * i + 2];
+        if (rows > 0) total += rows * g->plans[seg[3 * i]]->n;
+    }
+    const int64_t target = (total + kPipeChunks - 1) / kPipeChunks;
+    std::vector<std::vector<Piece>> chunks(1);
+    int64_t in_chunk = 0;
+    for (int i = 0; i < nseg; ++i) {
+        dctplus_plan_t p = g->plans[seg[3 * i]];
+        const int n = p->n;
+        int64_t off = seg[3 * i + 1], rows = seg[3 * i + 2];
+        while (rows > 0) {
+            if (in_chunk >= target && (int)chunks.size() < kPipeChunks) {
+                chunks.emplace_back();
+                in_chunk = 0;
+            }
+            int64_t take = rows;
+            const int64_t room = target - in_chunk;
+            if ((int)chunks.size() < kPipeChunks && rows * n > room) {
+                // cut at a whole tile of packed rows, at least one tile
+                const int64_t tiles = std::max<int64_t>(1, room / kPipeCut);
+                take = std::min<int64_t>(rows, tiles * kPipeCut / n);
+            }
+            chunks.back().push_back({p, off, take, take * n});
+            in_chunk += take * n;
+            off += take * n;
+            rows -= take;
+        }
+    }
+    cudaEvent_t done_up = g->pipe_events[2 * kPipeChunks];
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        // address ranges of this chunk, merged where pieces touch
+        std::vector<std::pair<int64_t, int64_t>> ranges;
+        for (const Piece& q : chunks[c]) {
+            if (!ranges.empty() && ranges.back().second == q.off) ranges.back().second = q.off + q.elems;
+            else ranges.push_back({q.off, q.off + q.elems});
+        }
+        for (auto& r : ranges)
+            DCTPLUS_CUDA_TRY(cudaMemcpyAsync(dx + r.first, x_host + r.first,
+                                             sizeof(float) * (r.second - r.first),
+                                             cudaMemcpyHostToDevice, up));
+        cudaEvent_t ev_up = g->pipe_events[2 * c], ev_k = g->pipe_events[2 * c + 1];
+        DCTPLUS_CUDA_TRY(cudaEventRecord(ev_up, up));
+        DCTPLUS_CUDA_TRY(cudaStreamWaitEvent(g->pipe_compute, ev_up, 0));
+        std::vector<TcSegHost> tc;
+        for (const Piece& q : chunks[c]) tc.push_back({q.p, dx + q.off, dy + q.off, q.rows});
+        dctplus_status st = launch_tc_segments(tc, g->pipe_compute, g->device);
+        if (st != DCTPLUS_OK) return st;
+        DCTPLUS_CUDA_TRY(cudaEventRecord(ev_k, g->pipe_compute));
+        DCTPLUS_CUDA_TRY(cudaStreamWaitEvent(g->pipe_d2h, ev_k, 0));
+        for (auto& r : ranges)
+            DCTPLUS_CUDA_TRY(cudaMemcpyAsync(y_host + r.first, dy + r.first,
+                                             sizeof(float) * (r.second - r.first),
+                                             cudaMemcpyDeviceToHost, g->pipe_d2h));
+    }
+    DCTPLUS_CUDA_TRY(cudaEventRecord(done_up, g->pipe_d2h));
+    DCTPLUS_CUDA_TRY(cudaStreamWaitEvent(up, done_up, 0));  // the caller's stream sees the result
+    DCTPLUS_CUDA_TRY(cudaStreamSynchronize(g->pipe_d2h));
+    DCTPLUS_CUDA_TRY(cudaStreamSynchronize(up));
+    return DCTPLUS_OK;
+}
+
 }  // namespace dctplus
 
 using namespace dctplus;
@@ -277,6 +365,9 @@ void dctplus_group_destroy(dctplus_group_t g) {
     if (g->d_seg) cudaFree(g->d_seg);
     if (g->d_tiles) cudaFree(g->d_tiles);
     if (g->d_stage) cudaFree(g->d_stage);
+    for (cudaEvent_t e : g->pipe_events) cudaEventDestroy(e);
+    if (g->pipe_compute) cudaStreamDestroy(g->pipe_compute);
+    if (g->pipe_d2h) cudaStreamDestroy(g->pipe_d2h);
     delete g;
 }
 
@@ -347,6 +438,11 @@ dctplus_status dctplus_execute_group_host(dctplus_group_t g, const float* x_host
     }
     float* dx = static_cast<float*>(g->d_stage);
     float* dy = reinterpret_cast<float*>(static_cast<char*>(g->d_stage) + half);
+    bool all_tc = true;
+    for (int i = 0; i < nseg; ++i)
+        if (seg_host[3 * i + 2] > 0 && !small_tc_capable(g->plans[seg_host[3 * i]])) all_tc = false;
+    if (all_tc && total_elems >= kPipeMinElems)
+        return group_host_pipelined(g, x_host, y_host, dx, dy, seg_host, nseg, s);
     DCTPLUS_CUDA_TRY(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, s));
     st = dctplus_execute_group(g, dx, dy, seg_host, nseg, stream);
     if (st != DCTPLUS_OK) return st;

@@ -98,6 +98,9 @@ struct dctplus_group_s {
     int ntiles = 0;
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
+    // streams and events of the pipelined host-buffer path (created on first use)
+    cudaStream_t pipe_compute = nullptr, pipe_d2h = nullptr;
+    std::vector<cudaEvent_t> pipe_events;
 };
 
 #define DCTPLUS_CUDA_TRY(expr)                                  \

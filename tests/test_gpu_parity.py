@@ -234,6 +234,20 @@ def test_mixed_size_full_workload_sampled(pkg):
     seg = np.array([[index[(s.n, s.update)], s.offset, s.rows] for s in wl.segments], dtype=np.int64)
     x = torch.tensor(wl.x, device="cuda")
     y = group.forward(x, seg).cpu().numpy()
+    # the host-buffer path runs in overlapped chunks at this size; same bytes as the device path
+    yh = group.forward_host(wl.x, seg)
+    assert np.array_equal(yh, y)
+    # segments given out of address order, with a gap left untouched in the output
+    order = np.arange(len(seg))[::-1]
+    gap = seg[3].copy()
+    seg2 = np.delete(seg[order], len(seg) - 1 - 3, axis=0)
+    yh2 = np.full_like(wl.x, 7.0)
+    yh2 = group.forward_host(wl.x, seg2, out=yh2)
+    lo, hi = gap[1], gap[1] + gap[2] * plans[gap[0]].n
+    assert np.all(yh2[lo:hi] == 7.0)
+    mask = np.ones(len(y), dtype=bool)
+    mask[lo:hi] = False
+    assert np.array_equal(yh2[mask], y[mask])
     rng = np.random.default_rng(11)
     for s in wl.segments:
         v, rho = wl.updates[s.n][s.update]
