@@ -126,7 +126,10 @@ int dctplus_plan_cauchy_mode(dctplus_plan_t plan);
 /* Forward transform of a batch (Algorithm 1; Theorem 3.1 eq. fwd_map):
  * y_b = X^T x_b for b = 0..batch-1.
  *   dtype : DCTPLUS_F32 (split-TF32 tensor-core contractions, FP32 in/out) or
- *           DCTPLUS_F64 (FP64 CUDA-core path, n <= 1024).
+ *           DCTPLUS_F64 (FP64 CUDA-core path, n <= 1024). FP32 takes every
+ *           n <= 4096 (lengths above 64 that are not powers of two run the
+ *           DCT-II and the Cauchy product as CUDA-core products with the plan's
+ *           tables) and powers of two up to 16384.
  *   x_dev, y_dev: device pointers aligned to the element size, rows of n
  *           elements with leading dimensions ldx, ldy >= n. The tensor-core
  *           kernels run when both bases are 16-byte aligned and ldx, ldy are
@@ -213,7 +216,8 @@ dctplus_status dctplus_backward(dctplus_plan_t plan, const float* gy_dev, int64_
  *   y_dev  : batch FP32 rows of nplans * m_out, leading dimension
  *            ldy >= nplans * m_out; row b holds y_0 | y_1 | ... (plan order).
  *   1 <= m_out <= c_p <= n. x and y must not overlap; 4-byte aligned.
- * n > 64 must be a power of two. The tensor-core contraction runs when
+ * n > 64 that is not a power of two (n <= 4096) uses CUDA-core products
+ * throughout. The tensor-core contraction runs when n > 64 is a power of two,
  * nplans * m_out is a multiple of 128, c_p a multiple of 32, y 16-byte aligned
  * and ldy a multiple of 4; otherwise the CUDA-core one.
  * The first call for a given (plans, m_out, c_p) builds and caches the stacked

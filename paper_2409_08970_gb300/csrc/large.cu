@@ -739,7 +739,16 @@ dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, f
         return launch_gemm_tc(ws, ws + plane, n, p->d_xthi, p->d_xtlo, n, y, ldy, (int)batch, n, n,
                               st, p->device);
     }
-    if (n & (n - 1)) return DCTPLUS_ERR_UNSUPPORTED;
+    if (n & (n - 1)) {
+        // no FFT length: the DCT-II and the Cauchy product as CUDA-core products with the
+        // plan's U^T and W tables (any n)
+        if (!p->d_ct32 || !p->d_w32) return DCTPLUS_ERR_UNSUPPORTED;
+        float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * plane));
+        if (!ws) return DCTPLUS_ERR_CUDA;
+        dctplus_status r = launch_rows_gemm(x, ldx, p->d_ct32, n, ws, n, batch, n, n, st);
+        if (r != DCTPLUS_OK) return r;
+        return launch_rows_gemm(ws, n, p->d_w32, n, y, ldy, batch, n, n, st);
+    }
     if (p->cauchy_mode == DCTPLUS_CAUCHY_HIER && y_ok) return launch_hier(p, x, ldx, y, ldy, batch, st);
     if (p->cauchy_mode == DCTPLUS_CAUCHY_DENSE && p->d_whi && y_ok) {
         // Algorithm 1 steps 1-2 (DCT-II, split for the tensor cores), then y = W s

@@ -445,9 +445,11 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
                                             p->d_whi, p->d_wlo);
         count_launch();
     }
-    if (n <= kF64Max) {
-        if (n <= kSmallMax) DCTPLUS_CUDA_TRY(dalloc(&p->d_ct32, nn));
-        DCTPLUS_CUDA_TRY(dalloc(&p->d_ct64, nn));
+    // U^T in FP32 for the small kernels and for lengths without an FFT (n > 64 not a power of two)
+    const bool want_ct32 = n <= kSmallMax || ((n & (n - 1)) != 0 && n <= kTableMax);
+    if (n <= kF64Max || want_ct32) {
+        if (want_ct32) DCTPLUS_CUDA_TRY(dalloc(&p->d_ct32, nn));
+        if (n <= kF64Max) DCTPLUS_CUDA_TRY(dalloc(&p->d_ct64, nn));
         k_ct_table<<<blocks_nn, 256, 0, s>>>(n, p->d_sin, p->d_ct32, p->d_ct64);
         count_launch();
     }

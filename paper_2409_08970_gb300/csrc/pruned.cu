@@ -246,7 +246,8 @@ extern "C" dctplus_status dctplus_execute_pruned(const dctplus_plan_t* plans, in
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return DCTPLUS_ERR_NO_DEVICE;
     if (cur != plans[0]->device) return DCTPLUS_ERR_INVALID_ARG;
-    if (n > kSmallMax && ((n & (n - 1)) || !plans[0]->d_twiddle)) return DCTPLUS_ERR_UNSUPPORTED;
+    const bool fft = n > kSmallMax && (n & (n - 1)) == 0 && plans[0]->d_twiddle;
+    if (!fft && !plans[0]->d_ct32) return DCTPLUS_ERR_UNSUPPORTED;
 
     PrunedSet* set = nullptr;
     dctplus_status st = get_set(plans, nplans, m_out, c_p, &set);
@@ -257,10 +258,10 @@ extern "C" dctplus_status dctplus_execute_pruned(const dctplus_plan_t* plans, in
     if (!s) return DCTPLUS_ERR_CUDA;
     float* s_lo = s + plane;
 
-    const bool tc = n > kSmallMax && width % 128 == 0 && width / 128 <= 128 && c_p % 32 == 0 &&
+    const bool tc = fft && width % 128 == 0 && width / 128 <= 128 && c_p % 32 == 0 &&
                     (reinterpret_cast<uintptr_t>(y_dev) & 15) == 0 && (ldy & 3) == 0;
     // Algorithm 1 step 1, once for all K updates
-    if (n > kSmallMax) {
+    if (fft) {
         st = launch_dct_fft(plans[0], x_dev, ldx, s, tc ? s_lo : nullptr, n, batch, cs);
     } else {
         st = launch_rows_gemm(x_dev, ldx, plans[0]->d_ct32, n, s, n, batch, n, n, cs);

@@ -78,7 +78,7 @@ def param_error_bounds(op, x, g):
     return b_rho, b_v
 
 
-@pytest.mark.parametrize("n,batch", [(16, 33), (48, 70), (64, 20), (256, 300), (1024, 256)])
+@pytest.mark.parametrize("n,batch", [(16, 33), (48, 70), (64, 20), (96, 40), (256, 300), (1024, 256)])
 def test_backward_matches_oracle_gradients(pkg, n, batch):
     for v, rho in [(random_unit_v(n, seed=1), 2.0), (random_unit_v(n, seed=2), -0.3)]:
         x = normal_signals(batch, n, seed=n)

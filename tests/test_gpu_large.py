@@ -136,3 +136,16 @@ def test_dense_mode_full_batch_sampled(pkg):
         assert pr.max() < 2e-6
         plan.close()
     assert pkg.dctplus_sync_check(0) == 0
+
+
+@pytest.mark.parametrize("n", [96, 100, 160, 384, 1000, 3000])
+def test_lengths_without_an_fft_match_oracle(pkg, n):
+    batch = 70
+    for v, rho in [(random_unit_v(n), -0.3), (edge_update_v(n, n // 2 - 1, n // 2), 1.5)]:
+        x = normal_signals(batch, n, seed=n)
+        ref = cauchy.transform(cauchy.make_plan(n, v, rho), x)
+        plan = pkg.Plan(n, v, rho)
+        err = relerr(run32(plan, x), ref)
+        assert err.max() < F32_TOL, (n, rho, err.max())
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0

@@ -84,7 +84,7 @@ def test_pruned_cuda_core_path_and_mixed_updates(pkg):
     assert pkg.dctplus_sync_check(0) == 0
 
 
-@pytest.mark.parametrize("n", [8, 32, 64])
+@pytest.mark.parametrize("n", [8, 32, 64, 96])
 def test_pruned_small_n(pkg, n):
     vs = [(self_loop_v(n, 0), 0.5), (random_unit_v(n, seed=2), -0.5)]
     plans = [pkg.Plan(n, v, r) for v, r in vs]
