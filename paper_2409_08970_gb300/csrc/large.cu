@@ -23,35 +23,31 @@ namespace dctplus {
 
 __constant__ float2 c_tw64[64];  // exp(-2 pi i j / 64)
 
-// Four-step split M = M1 x M2 of the length-M complex FFT (M1, M2 <= 64), for
-// n <= 8192; 0 for larger n (the Stockham kernel handles those).
-__host__ __device__ inline int dct_split_m1(int n) {
-    switch (n) {
-        case 128: return 8;
-        case 256: return 16;
-        case 512: return 16;
-        case 1024: return 32;
-        case 2048: return 32;
-        case 4096: return 64;
-        case 8192: return 64;
-        default: return 0;
-    }
-}
+// Radix of the in-place decimation-in-frequency pass on blocks of B points:
+// 8 while B is a multiple of 8, then 4 or 2 for what is left.
+__host__ __device__ constexpr int fft_radix(int B) { return B % 8 == 0 ? 8 : (B % 4 == 0 ? 4 : 2); }
 
 // twiddles: [0, M): exp(-2 pi i j / M); [M, 2M + 1): exp(-2 pi i k / n), k = 0..M;
-// [2M + 1, 3M + 2): c_k exp(-i pi k / 2n), k = 0..M; [3M + 2, 4M + 2): the
-// four-step twiddles exp(-2 pi i k1 n2 / M) at k1 * M2 + n2   (M = n / 2)
+// [2M + 1, 3M + 2): c_k exp(-i pi k / 2n), k = 0..M; from 3M + 2: for each pass
+// of the in-place FFT (block B, radix R, stride S = B / R), B entries
+// exp(-2 pi i n1 k2 / B) at k2 * S + n1   (M = n / 2)
 __global__ void k_fft_tables(int n, float2* tw) {
     int M = n / 2;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 3 * M + 2 && idx < 4 * M + 2) {
-        const int e = idx - (3 * M + 2);
-        const int m1 = dct_split_m1(n), m2 = m1 ? M / m1 : 1;
-        const int k1 = e / m2, n2 = e % m2;
-        const long long prod = (long long)k1 * n2 % M;  // reduce the phase exactly
-        double s, c;
-        sincospi(-2.0 * (double)prod / M, &s, &c);
-        tw[idx] = make_float2((float)c, (float)s);
+    if (idx >= 3 * M + 2 && idx < 5 * M + 2) {
+        int e = idx - (3 * M + 2);
+        for (int B = M; B > 1; B /= fft_radix(B)) {
+            if (e < B) {
+                const int S = B / fft_radix(B), k2 = e / S, n1 = e % S;
+                const long long prod = (long long)n1 * k2 % B;  // reduce the phase exactly
+                double s, c;
+                sincospi(-2.0 * (double)prod / B, &s, &c);
+                tw[idx] = make_float2((float)c, (float)s);
+                return;
+            }
+            e -= B;
+        }
+        tw[idx] = make_float2(0.f, 0.f);
     } else if (idx < M) {
         double s, c;
         sincospi(-2.0 * idx / M, &s, &c);
@@ -74,7 +70,7 @@ dctplus_status setup_large(dctplus_plan_t p) {
     int n = p->n;
     if (n & (n - 1)) return DCTPLUS_OK;  // FFT path only for powers of two
     int M = n / 2;
-    size_t cnt = 4 * M + 2;
+    size_t cnt = 5 * M + 2;
     DCTPLUS_CUDA_TRY(cudaMalloc((void**)&p->d_twiddle, sizeof(float2) * cnt));
     k_fft_tables<<<(int)((cnt + 255) / 256), 256>>>(n, reinterpret_cast<float2*>(p->d_twiddle));
     count_launch();
@@ -235,67 +231,76 @@ __device__ __forceinline__ void dft_reg(float2 (&a)[R]) {
     for (int i = 0; i < R; ++i) a[i] = t[i];
 }
 
-// Length-M DFT of buf[0..M) (natural order) in place, by the four-step split
-// M = M1 M2 with M2 threads per signal (thread t); the result is left in
-// natural order in buf[0..M). buf holds M1 (M2 + 1) float2 (the padded
-// matrix). Contains __syncthreads: every thread of the CTA must call it.
-template <int M1, int M2>
-__device__ __forceinline__ void fft4_core(float2* buf, int t, const float2* __restrict__ tw4) {
-    constexpr int TPS = M2;
-    {  // column t: DFT over n1 of w[t + M2 n1], then the twiddles
-        float2 a[M1];
-#pragma unroll
-        for (int i = 0; i < M1; ++i) a[i] = buf[t + M2 * i];
-        dft_reg<M1>(a);
-#pragma unroll
-        for (int k1 = 1; k1 < M1; ++k1) a[k1] = cmul(a[k1], __ldg(tw4 + k1 * M2 + t));
-        __syncthreads();
-#pragma unroll
-        for (int k1 = 0; k1 < M1; ++k1) buf[k1 * (M2 + 1) + t] = a[k1];
-    }
-    __syncthreads();
-    float2 b[M1 / M2][M2];
-#pragma unroll
-    for (int r = 0; r < M1 / M2; ++r) {  // rows k1 = t + r M2: DFT over n2
-        const int k1 = t + r * TPS;
-#pragma unroll
-        for (int i = 0; i < M2; ++i) b[r][i] = buf[k1 * (M2 + 1) + i];
-        dft_reg<M2>(b[r]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < M1 / M2; ++r) {
-        const int k1 = t + r * TPS;
-#pragma unroll
-        for (int k2 = 0; k2 < M2; ++k2) buf[k1 + M1 * k2] = b[r][k2];  // X[k1 + M1 k2]
-    }
-    __syncthreads();
+// Shared-memory index of point i of a signal's buffer: one pad slot every 8
+// points keeps the strided accesses of every pass free of bank conflicts.
+__device__ __forceinline__ int fft_phys(int i) { return i + (i >> 3); }
+
+__host__ __device__ constexpr int fft_tw_offset(int M, int B) {
+    int off = 0;
+    for (int b = M; b > B; b /= fft_radix(b)) off += b;
+    return off;
 }
 
-// DCT-II by Makhoul's reordering and a four-step FFT of length M = M1 M2
-// (M1 >= M2): M2 in-register DFTs of length M1 over the strided columns, the
-// twiddles exp(-2 pi i k1 n2 / M), then M1 in-register DFTs of length M2 over
-// the rows of a padded (conflict-free) shared-memory matrix. M2 threads per
-// signal: thread t owns column t in the first step and rows t, t + M2, ... in
-// the second, so no lane idles. Several signals per CTA. Loads are float4
-// (when aligned) and the stores of s (and its TF32 remainder s_lo) are four
-// coalesced streams.
-template <int M1, int M2>
-__global__ void __launch_bounds__(256, M1 >= 64 ? 1 : 2) k_dct_4step(int n, const float* __restrict__ x, int64_t ldx,
-                                                      float* __restrict__ s, float* __restrict__ s_lo,
-                                                      int64_t lds, int64_t batch,
-                                                      const float2* __restrict__ tw, int vec) {
-    static_assert(M1 >= M2 && M1 % M2 == 0, "four-step split needs M1 >= M2");
-    constexpr int M = M1 * M2;
-    constexpr int TPS = M2;
-    constexpr int BUF = M1 * (M2 + 1);  // float2 per signal (>= M)
+// One in-place decimation-in-frequency pass on blocks of B points, radix R:
+// butterfly (b, n1) takes the R points b B + n1 + r S (S = B / R), a length-R
+// DFT in registers, twiddles exp(-2 pi i n1 k2 / B), and puts output k2 back at
+// b B + n1 + k2 S. Each thread writes exactly the points it read.
+template <int M, int B>
+__device__ __forceinline__ void fft_pass(float2* buf, int t, const float2* __restrict__ twp) {
+    constexpr int R = fft_radix(B), S = B / R, TPS = M / 8, PER = (M / R) / TPS;
+    const float2* tw = twp + fft_tw_offset(M, B);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int u = t + j * TPS, b = u / S, n1 = u % S, base = b * B + n1;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[fft_phys(base + r * S)];
+        dft_reg<R>(v);
+        if (S > 1) {
+#pragma unroll
+            for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], __ldg(tw + k2 * S + n1));
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < R; ++k2) buf[fft_phys(base + k2 * S)] = v[k2];
+    }
+    __syncthreads();
+    if constexpr (S > 1) fft_pass<M, S>(buf, t, twp);
+}
+
+// Position of output k after all passes (mixed-radix digit reversal)
+template <int M>
+__device__ __forceinline__ int fft_out_pos(int k) {
+    int pos = 0, kk = k;
+    int Bc = M;
+#pragma unroll
+    for (int B = M; B > 1; B /= fft_radix(B)) {
+        const int R = fft_radix(B);
+        Bc /= R;
+        pos += (kk % R) * Bc;
+        kk /= R;
+    }
+    return pos;
+}
+
+// DCT-II by Makhoul's reordering and an in-place mixed-radix FFT of length
+// M = n / 2 in shared memory (radix-8 passes, M / 8 threads per signal, each
+// butterfly's points in registers), then the split and post-twiddle. Several
+// signals per CTA. Loads are float4 (when aligned) and the stores of s (and its
+// TF32 remainder s_lo) are four coalesced streams.
+template <int M>
+__global__ void __launch_bounds__(512) k_dct_r8(int n, const float* __restrict__ x, int64_t ldx,
+                                                float* __restrict__ s, float* __restrict__ s_lo,
+                                                int64_t lds, int64_t batch,
+                                                const float2* __restrict__ tw, int vec) {
+    constexpr int TPS = M / 8;
+    constexpr int BUF = M + M / 8;  // float2 per signal
     extern __shared__ __align__(16) float2 dsm[];
     const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
     const int spc = blockDim.x / TPS;
     float2* buf = dsm + slot * BUF;
     const float2* __restrict__ tw_split = tw + M;
     const float2* __restrict__ tw_post = tw + 2 * M + 1;
-    const float2* __restrict__ tw4 = tw + 3 * M + 2;
+    const float2* __restrict__ twp = tw + 3 * M + 2;
     for (int64_t base = (int64_t)blockIdx.x * spc; base < batch; base += (int64_t)gridDim.x * spc) {
         const int64_t sig = base + slot;
         const bool live = sig < batch;
@@ -303,36 +308,32 @@ __global__ void __launch_bounds__(256, M1 >= 64 ? 1 : 2) k_dct_4step(int n, cons
         if (live) {  // w_q = x_4q + i x_4q+2, w_{M-1-q} = x_4q+3 + i x_4q+1 (Makhoul order)
             const float* xs = x + sig * ldx;
             constexpr int kLoads = M / 2 / TPS;
+            float4 v[kLoads];
 #pragma unroll
-            for (int h = 0; h < kLoads; h += 8) {  // at most 8 float4 in flight per thread
-                float4 v[8];
+            for (int i = 0; i < kLoads; ++i) {
+                const int q = t + i * TPS;
+                if (vec) v[i] = __ldg(reinterpret_cast<const float4*>(xs) + q);
+                else v[i] = make_float4(xs[4 * q], xs[4 * q + 1], xs[4 * q + 2], xs[4 * q + 3]);
+            }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (h + i >= kLoads) break;
-                    const int q = t + (h + i) * TPS;
-                    if (vec) v[i] = __ldg(reinterpret_cast<const float4*>(xs) + q);
-                    else v[i] = make_float4(xs[4 * q], xs[4 * q + 1], xs[4 * q + 2], xs[4 * q + 3]);
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (h + i >= kLoads) break;
-                    const int q = t + (h + i) * TPS;
-                    buf[q] = make_float2(v[i].x, v[i].z);
-                    buf[M - 1 - q] = make_float2(v[i].w, v[i].y);
-                }
+            for (int i = 0; i < kLoads; ++i) {
+                const int q = t + i * TPS;
+                buf[fft_phys(q)] = make_float2(v[i].x, v[i].z);
+                buf[fft_phys(M - 1 - q)] = make_float2(v[i].w, v[i].y);
             }
         }
         __syncthreads();
-        fft4_core<M1, M2>(buf, t, tw4);
+        fft_pass<M, M>(buf, t, twp);
         if (!live) continue;
         float* ss = s + sig * lds;
         float* sl = s_lo ? s_lo + sig * lds : nullptr;
         constexpr int kPost = (M / 2 + TPS) / TPS;  // covers k = 0 .. M / 2
-#pragma unroll 4
+#pragma unroll
         for (int i = 0; i < kPost; ++i) {
             const int k = t + i * TPS;
             if (k > M / 2) break;
-            const float2 xk = buf[k], xm = buf[(M - k) & (M - 1)];
+            const float2 xk = buf[fft_phys(fft_out_pos<M>(k))];
+            const float2 xm = buf[fft_phys(fft_out_pos<M>((M - k) & (M - 1)))];
             const float2 fe = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
             const float2 fo = make_float2(0.5f * (xk.y + xm.y), -0.5f * (xk.x - xm.x));  // (xk - conj xm) / 2i
             float2 tt = cmul(__ldg(tw_split + k), fo);
@@ -358,57 +359,68 @@ __global__ void __launch_bounds__(256, M1 >= 64 ? 1 : 2) k_dct_4step(int n, cons
     }
 }
 
-template <int M1, int M2>
-static dctplus_status launch_4step(int n, const float* x, int64_t ldx, float* s_out, float* s_lo,
-                                   int64_t lds, int64_t batch, const float2* tw, int vec,
-                                   cudaStream_t st, int dev) {
-    constexpr int TPS = M2;
-    constexpr size_t kBufBytes = sizeof(float2) * M1 * (M2 + 1);
+// CTA shape for the radix-8 kernels: M / 8 threads per signal, up to 256 threads,
+// but small batches spread over all SMs
+template <int M>
+static void r8_shape(int64_t batch, int dev, int* spc_out, size_t* smem_out, int64_t* grid_out) {
+    constexpr int TPS = M / 8;
+    constexpr size_t kBufBytes = sizeof(float2) * (M + M / 8);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     sms = std::max(sms, 1);
-    // signals per CTA: up to 256 threads, but spread small batches over all SMs
-    int spc = 256 / TPS;
+    int spc = std::max(1, 256 / TPS);
     while (spc > 1 && (spc * kBufBytes > 96 * 1024 || (batch + spc - 1) / spc < 4LL * sms)) spc >>= 1;
     const size_t smem = spc * kBufBytes;
-    if (smem > 48 * 1024) {
-        static bool attr[64] = {};
-        if (!attr[dev & 63]) {
-            DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_4step<M1, M2>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-            attr[dev & 63] = true;
-        }
-    }
     const int threads = spc * TPS;
     const int per_sm = std::max(1, std::min({(int)(200 * 1024 / smem), 2048 / threads, 32}));
     const int64_t groups = (batch + spc - 1) / spc;
-    const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
-    k_dct_4step<M1, M2><<<(unsigned)grid, threads, smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec);
+    *spc_out = spc;
+    *smem_out = smem;
+    *grid_out = std::min<int64_t>(groups, (int64_t)sms * per_sm);
+}
+
+template <int M>
+static dctplus_status launch_r8(int n, const float* x, int64_t ldx, float* s_out, float* s_lo,
+                                int64_t lds, int64_t batch, const float2* tw, int vec,
+                                cudaStream_t st, int dev) {
+    int spc;
+    size_t smem;
+    int64_t grid;
+    r8_shape<M>(batch, dev, &spc, &smem, &grid);
+    if (smem > 48 * 1024) {
+        static bool attr[64] = {};
+        if (!attr[dev & 63]) {
+            DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_r8<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  200 * 1024));
+            attr[dev & 63] = true;
+        }
+    }
+    k_dct_r8<M><<<(unsigned)grid, spc * (M / 8), smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec);
     count_launch();
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
 
-// Inverse of k_dct_4step (DCT-III, x = U s, orthonormal): undo the post-twiddle
+// Inverse of k_dct_r8 (DCT-III, x = U s, orthonormal): undo the post-twiddle
 // (B_k = s_k - i s_{n-k}, V_k = B_k exp(i pi k / 2n) / c_k), undo the real
 // split (X_k = Fe_k + i Fo_k with Fe_k = (V_k + conj V_{M-k}) / 2 and
 // Fo_k = (V_k - conj V_{M-k}) exp(2 pi i k / n) / 2), then the inverse DFT as
-// conj(DFT(conj X)) / M on the same four-step core, and Makhoul's order back
-// to x with float4 stores.
-template <int M1, int M2>
-__global__ void __launch_bounds__(256, M1 >= 64 ? 1 : 2) k_idct_4step(int n, const float* __restrict__ s, int64_t lds,
-                                                       float* __restrict__ x, int64_t ldx,
-                                                       int64_t batch, const float2* __restrict__ tw, int vec) {
-    constexpr int M = M1 * M2;
-    constexpr int TPS = M2;
-    constexpr int BUF = M1 * (M2 + 1);
+// conj(DFT(conj X)) / M with the same passes, and Makhoul's order back to x
+// with float4 stores. X enters the passes in natural order and leaves in the
+// passes' digit-reversed order.
+template <int M>
+__global__ void __launch_bounds__(512) k_idct_r8(int n, const float* __restrict__ s, int64_t lds,
+                                                 float* __restrict__ x, int64_t ldx, int64_t batch,
+                                                 const float2* __restrict__ tw, int vec) {
+    constexpr int TPS = M / 8;
+    constexpr int BUF = M + M / 8;
     extern __shared__ __align__(16) float2 dsm[];
     const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
     const int spc = blockDim.x / TPS;
     float2* buf = dsm + slot * BUF;
     const float2* __restrict__ tw_split = tw + M;
     const float2* __restrict__ tw_post = tw + 2 * M + 1;
-    const float2* __restrict__ tw4 = tw + 3 * M + 2;
+    const float2* __restrict__ twp = tw + 3 * M + 2;
     const float scale0 = (float)n, scale = 0.5f * (float)n;  // 1 / c_k^2
     for (int64_t base = (int64_t)blockIdx.x * spc; base < batch; base += (int64_t)gridDim.x * spc) {
         const int64_t sig = base + slot;
@@ -417,12 +429,11 @@ __global__ void __launch_bounds__(256, M1 >= 64 ? 1 : 2) k_idct_4step(int n, con
         if (live) {
             const float* ss = s + sig * lds;
             constexpr int kPre = (M / 2 + TPS) / TPS;
-#pragma unroll 4
+#pragma unroll
             for (int i = 0; i < kPre; ++i) {
                 const int k = t + i * TPS;
                 if (k > M / 2) break;
                 const int kp = M - k;
-                // V_k and V_{M-k}
                 const float2 bk = k == 0 ? make_float2(ss[0], 0.f) : make_float2(ss[k], -ss[n - k]);
                 const float2 bm = kp == M ? make_float2(ss[M], -ss[M]) : make_float2(ss[kp], -ss[n - kp]);
                 const float2 pk = __ldg(tw_post + k), pm = __ldg(tw_post + kp);
@@ -435,26 +446,26 @@ __global__ void __launch_bounds__(256, M1 >= 64 ? 1 : 2) k_idct_4step(int n, con
                 const float2 d = make_float2(vk.x - vm.x, vk.y + vm.y);  // vk - conj vm
                 const float2 wk = __ldg(tw_split + k);
                 const float2 fo = cmul(make_float2(0.5f * d.x, 0.5f * d.y), make_float2(wk.x, -wk.y));
-                // conj(X_k), X_k = fe + i fo
-                buf[k] = make_float2(fe.x - fo.y, -(fe.y + fo.x));
+                buf[fft_phys(k)] = make_float2(fe.x - fo.y, -(fe.y + fo.x));  // conj(X_k)
                 if (kp != k && kp < M) {
                     const float2 wm = __ldg(tw_split + kp);
                     // fe' = conj fe, fo' = -conj(d) exp(2 pi i kp / n) / 2
                     const float2 fo2 = cmul(make_float2(-0.5f * d.x, 0.5f * d.y), make_float2(wm.x, -wm.y));
-                    buf[kp] = make_float2(fe.x - fo2.y, -(-fe.y + fo2.x));
+                    buf[fft_phys(kp)] = make_float2(fe.x - fo2.y, -(-fe.y + fo2.x));
                 }
             }
         }
         __syncthreads();
-        fft4_core<M1, M2>(buf, t, tw4);
+        fft_pass<M, M>(buf, t, twp);
         if (!live) continue;
         float* xs = x + sig * ldx;
         const float inv = 1.0f / (float)M;
         constexpr int kStores = M / 2 / TPS;
-#pragma unroll 4
+#pragma unroll
         for (int i = 0; i < kStores; ++i) {
             const int q = t + i * TPS;
-            const float2 a = buf[q], b2 = buf[M - 1 - q];  // w = conj(buf) / M
+            const float2 a = buf[fft_phys(fft_out_pos<M>(q))];           // w = conj(buf) / M
+            const float2 b2 = buf[fft_phys(fft_out_pos<M>(M - 1 - q))];
             const float4 v = make_float4(a.x * inv, -b2.y * inv, -a.y * inv, b2.x * inv);
             if (vec) {
                 reinterpret_cast<float4*>(xs)[q] = v;
@@ -468,30 +479,22 @@ __global__ void __launch_bounds__(256, M1 >= 64 ? 1 : 2) k_idct_4step(int n, con
     }
 }
 
-template <int M1, int M2>
-static dctplus_status launch_i4step(int n, const float* s, int64_t lds, float* x, int64_t ldx,
-                                    int64_t batch, const float2* tw, int vec, cudaStream_t st, int dev) {
-    constexpr int TPS = M2;
-    constexpr size_t kBufBytes = sizeof(float2) * M1 * (M2 + 1);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    sms = std::max(sms, 1);
-    int spc = 256 / TPS;
-    while (spc > 1 && (spc * kBufBytes > 96 * 1024 || (batch + spc - 1) / spc < 4LL * sms)) spc >>= 1;
-    const size_t smem = spc * kBufBytes;
+template <int M>
+static dctplus_status launch_ir8(int n, const float* s, int64_t lds, float* x, int64_t ldx,
+                                 int64_t batch, const float2* tw, int vec, cudaStream_t st, int dev) {
+    int spc;
+    size_t smem;
+    int64_t grid;
+    r8_shape<M>(batch, dev, &spc, &smem, &grid);
     if (smem > 48 * 1024) {
         static bool attr[64] = {};
         if (!attr[dev & 63]) {
-            DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_idct_4step<M1, M2>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_idct_r8<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  200 * 1024));
             attr[dev & 63] = true;
         }
     }
-    const int threads = spc * TPS;
-    const int per_sm = std::max(1, std::min({(int)(200 * 1024 / smem), 2048 / threads, 32}));
-    const int64_t groups = (batch + spc - 1) / spc;
-    const int64_t grid = std::min<int64_t>(groups, (int64_t)sms * per_sm);
-    k_idct_4step<M1, M2><<<(unsigned)grid, threads, smem, st>>>(n, s, lds, x, ldx, batch, tw, vec);
+    k_idct_r8<M><<<(unsigned)grid, spc * (M / 8), smem, st>>>(n, s, lds, x, ldx, batch, tw, vec);
     count_launch();
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
@@ -505,13 +508,13 @@ dctplus_status launch_idct_fft(dctplus_plan_t p, const float* s, int64_t lds, fl
     const int vec4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
     const float2* tw = reinterpret_cast<const float2*>(p->d_twiddle);
     switch (n) {
-        case 128: return launch_i4step<8, 8>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
-        case 256: return launch_i4step<16, 8>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
-        case 512: return launch_i4step<16, 16>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
-        case 1024: return launch_i4step<32, 16>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
-        case 2048: return launch_i4step<32, 32>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
-        case 4096: return launch_i4step<64, 32>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
-        case 8192: return launch_i4step<64, 64>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 128: return launch_ir8<64>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 256: return launch_ir8<128>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 512: return launch_ir8<256>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 1024: return launch_ir8<512>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 2048: return launch_ir8<1024>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 4096: return launch_ir8<2048>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 8192: return launch_ir8<4096>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
         default: return DCTPLUS_ERR_UNSUPPORTED;
     }
 }
@@ -525,13 +528,13 @@ dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, flo
         const int vec4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
         const float2* tw = reinterpret_cast<const float2*>(p->d_twiddle);
         switch (n) {
-            case 128: return launch_4step<8, 8>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 256: return launch_4step<16, 8>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 512: return launch_4step<16, 16>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 1024: return launch_4step<32, 16>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 2048: return launch_4step<32, 32>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 4096: return launch_4step<64, 32>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 8192: return launch_4step<64, 64>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 128: return launch_r8<64>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 256: return launch_r8<128>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 512: return launch_r8<256>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 1024: return launch_r8<512>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 2048: return launch_r8<1024>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 4096: return launch_r8<2048>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 8192: return launch_r8<4096>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
             default: break;
         }
     }
