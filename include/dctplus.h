@@ -51,7 +51,7 @@ typedef struct CUstream_st* dctplus_stream_t; /* same handle as cudaStream_t */
 typedef enum {
     DCTPLUS_OK = 0,
     DCTPLUS_ERR_INVALID_ARG = 1,   /* bad size, pointer, stride or non-finite input */
-    DCTPLUS_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+    DCTPLUS_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement */
     DCTPLUS_ERR_NOT_CONVERGED = 3, /* secular root iteration hit its cap */
     DCTPLUS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     DCTPLUS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
