@@ -705,6 +705,7 @@ dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, 
 }
 
 // hi copy and TF32 remainder of a row-major batch (dense-GFT baseline input)
+// (hi may be null: the product then reads x itself as the hi operand)
 __global__ void k_split_rows(const float* __restrict__ x, int64_t ldx, int n, int64_t batch,
                              float* __restrict__ hi, float* __restrict__ lo) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -713,7 +714,7 @@ __global__ void k_split_rows(const float* __restrict__ x, int64_t ldx, int n, in
         int64_t b = idx / n;
         int j = (int)(idx % n);
         float v = x[b * ldx + j];
-        hi[idx] = v;
+        if (hi) hi[idx] = v;
         lo[idx] = tf32_lo(v);
     }
 }
@@ -732,15 +733,17 @@ dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, f
     const bool y_ok = (reinterpret_cast<uintptr_t>(y) & 15) == 0 && (ldy & 3) == 0;
     const size_t plane = (size_t)batch * n;
     if (p->cauchy_mode == DCTPLUS_CAUCHY_DENSE_GFT && y_ok) {
-        // comparison baseline: y = (x_hi + x_lo)(X^T_hi + X^T_lo)^T in one dense product
+        // comparison baseline: y = (x_hi + x_lo)(X^T_hi + X^T_lo)^T in one dense product;
+        // x itself is the hi operand when its layout allows, so only x_lo is written
+        const bool x_ok = (reinterpret_cast<uintptr_t>(x) & 15) == 0 && ldx == n;  // same ld as x_lo
         float* ws = static_cast<float*>(plan_workspace(p, st, 2 * sizeof(float) * plane));
         if (!ws) return DCTPLUS_ERR_CUDA;
         int64_t blocks = std::min<int64_t>((int64_t)((plane + 255) / 256), 152 * 16);
-        k_split_rows<<<(unsigned)blocks, 256, 0, st>>>(x, ldx, n, batch, ws, ws + plane);
+        k_split_rows<<<(unsigned)blocks, 256, 0, st>>>(x, ldx, n, batch, x_ok ? nullptr : ws, ws + plane);
         count_launch();
         DCTPLUS_CUDA_TRY(cudaGetLastError());
-        return launch_gemm_tc(ws, ws + plane, n, p->d_xthi, p->d_xtlo, n, y, ldy, (int)batch, n, n,
-                              st, p->device);
+        return launch_gemm_tc(x_ok ? x : ws, ws + plane, x_ok ? ldx : n, p->d_xthi, p->d_xtlo, n, y,
+                              ldy, (int)batch, n, n, st, p->device);
     }
     if (n & (n - 1)) {
         // no FFT length: the DCT-II and the Cauchy product as CUDA-core products with the
