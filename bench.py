@@ -518,13 +518,45 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the n=1024 and comparator items")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--quick", action="store_true", help="only the n=1024 large-n item")
+    ap.add_argument("--only", choices=["n256", "n1024", "n4096", "n16384", "pruned", "backward"],
+                    help="run just this secondary line (for profiling one kernel family); prints "
+                         "its JSON object alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args)
+
+
+def run_only(args):
+    """One secondary line without the headline step (profiling aid)."""
+    import torch
+    import paper_2409_08970_gb300 as pkg
+    from paper_2409_08970_gb300 import build as _build
+    _build.build()
+    hbm_peak, _, _ = load_peaks()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    D, H, G = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT
+    large = {"n256": (256, 4096, [H, D, G]), "n1024": (1024, 4096, [H, D, G]),
+             "n4096": (4096, 4096, [H, D, G]), "n16384": (16384, 512, [H])}
+    if args.only in large:
+        n, batch, modes = large[args.only]
+        out = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, n, batch, modes)
+    elif args.only == "pruned":
+        out = bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak)
+    else:
+        out = bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak)
+    print(json.dumps({args.only: out}), flush=True)
 
 
 if __name__ == "__main__":
