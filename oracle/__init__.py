@@ -14,9 +14,11 @@ Two independent evaluations of the same transform y = X^T x:
   Lemma 4.1 brackets, normalisation, and the Cauchy sum.
 * ``gradient``: derivatives of the transform with respect to the signal, rho and
   v (inverse transform; first-order eigenvector perturbation).
+* ``nfst_route``: the paper's own evaluation of the Cauchy product (pre-processing,
+  DST-I, trigonometric series over sin(n theta)), with a direct sum in place of the NFST.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force at n <= 8, O1 against O2).
 """
-from . import cauchy, common, definition, gradient  # noqa: F401
+from . import cauchy, common, definition, gradient, nfst_route  # noqa: F401
 from ._native import build as build_native  # noqa: F401
