@@ -71,10 +71,18 @@ typedef enum {
     DCTPLUS_CAUCHY_HIER = 2,  /* O(n log n) hierarchical far-field expansion (Theorem 3.2) */
     DCTPLUS_CAUCHY_SIMT = 3,  /* CUDA-core product, W from a stored table (n <= 4096) or
                                  generated tile by tile in shared memory */
-    DCTPLUS_CAUCHY_DENSE_GFT = 4 /* comparison baseline, not the factored method: one dense
+    DCTPLUS_CAUCHY_DENSE_GFT = 4, /* comparison baseline, not the factored method: one dense
                                     tensor-core product with the full X^T (n % 128 == 0,
                                     n <= 4096; X^T built in FP64 up to n = 1024, beyond that
                                     as W U^T on the tensor cores) */
+    DCTPLUS_CAUCHY_NFST = 5       /* the paper's own route (Algorithm 1 steps 3-7): the zero
+                                    pole's column kept explicit, a DST-I to the Chebyshev
+                                    coefficients, and the sine series over sin(n theta)
+                                    evaluated directly (Clenshaw) instead of by an NFST; FP64
+                                    inside for both dtypes, n <= 1024, O(n^2) per signal.
+                                    Loses accuracy like eps / |sin(n theta)| when a root sits
+                                    next to a pole. Used by dctplus_execute only; groups,
+                                    pruned and backward calls use their own kernels. */
 } dctplus_cauchy_mode;
 
 typedef struct {

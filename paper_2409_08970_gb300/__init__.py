@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    CAUCHY_AUTO, CAUCHY_DENSE, CAUCHY_DENSE_GFT, CAUCHY_HIER, CAUCHY_SIMT, ERR_SCRATCH_LIMIT, F32, F64,
+    CAUCHY_AUTO, CAUCHY_DENSE, CAUCHY_DENSE_GFT, CAUCHY_HIER, CAUCHY_NFST, CAUCHY_SIMT, ERR_SCRATCH_LIMIT,
+    F32, F64,
     SEG_WORDS, DctPlusError, Opts,
     check,
 )

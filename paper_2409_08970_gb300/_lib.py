@@ -29,6 +29,7 @@ CAUCHY_DENSE = 1
 CAUCHY_HIER = 2
 CAUCHY_SIMT = 3
 CAUCHY_DENSE_GFT = 4
+CAUCHY_NFST = 5
 
 SEG_WORDS = 3
 

@@ -208,7 +208,7 @@ dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, do
     dctplus_opts o{};
     o.device = -1;
     if (opts) o = *opts;
-    if (o.cauchy_mode < 0 || o.cauchy_mode > DCTPLUS_CAUCHY_DENSE_GFT || o.max_secular_iter < 0)
+    if (o.cauchy_mode < 0 || o.cauchy_mode > DCTPLUS_CAUCHY_NFST || o.max_secular_iter < 0)
         return DCTPLUS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DCTPLUS_ERR_NO_DEVICE;
@@ -293,6 +293,13 @@ dctplus_status dctplus_execute(dctplus_plan_t p, dctplus_dtype dtype, const void
     if ((st = check_device(p->device)) != DCTPLUS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int n = p->n;
+    if (p->cauchy_mode == DCTPLUS_CAUCHY_NFST) {  // the paper's trigonometric route, FP64 inside
+        if (dtype == DCTPLUS_F64)
+            return launch_nfst<double>(p, static_cast<const double*>(x_dev), ldx,
+                                       static_cast<double*>(y_dev), ldy, batch, s);
+        return launch_nfst<float>(p, static_cast<const float*>(x_dev), ldx, static_cast<float*>(y_dev),
+                                  ldy, batch, s);
+    }
     if (dtype == DCTPLUS_F64) {
         if (n > kF64Max) return DCTPLUS_ERR_UNSUPPORTED;
         if (n > kSmallMax)

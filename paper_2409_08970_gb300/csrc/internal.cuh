@@ -56,7 +56,7 @@ struct dctplus_plan_s {
 
     // device tables
     double* d_z = nullptr;         // n
-    double* d_sin = nullptr;       // 2n+1: sin(pi m / 2n)
+    double* d_sin = nullptr;       // n+1: sin(pi m / 2n), m = 0..n
     double* d_row_tau = nullptr;   // n
     double* d_row_a = nullptr;     // n
     int* d_row_kind = nullptr;     // n
@@ -79,6 +79,10 @@ struct dctplus_plan_s {
     dctplus::SmallTcTables tc;
     dctplus::HierTables* hier = nullptr;
     dctplus::BackwardTables* bwd = nullptr;  // built on the first dctplus_backward call
+    // the paper's trigonometric route (cauchy mode DCTPLUS_CAUCHY_NFST)
+    int* d_nfst_kind = nullptr;
+    void* d_nfst_rows = nullptr;
+    double* d_nfst_znd = nullptr;
 
     // staging for dctplus_execute_host
     void* d_stage = nullptr;
@@ -143,6 +147,12 @@ dctplus_status launch_rows_gemm(const float* a, int64_t lda, const float* w, int
 
 // backward.cu
 void free_backward(BackwardTables* b);
+
+// nfst.cu
+dctplus_status setup_nfst(dctplus_plan_t p);
+template <typename T>
+dctplus_status launch_nfst(dctplus_plan_t p, const T* x, int64_t ldx, T* y, int64_t ldy, int64_t batch,
+                           cudaStream_t st);
 
 // small_simt.cu
 dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,

@@ -282,7 +282,8 @@ void free_plan_tables(dctplus_plan_t p) {
     void* ptrs[] = {p->d_z, p->d_sin, p->d_row_tau, p->d_row_a, p->d_row_kind, p->d_row_pole,
                     p->d_ct32, p->d_ct64, p->d_w32, p->d_w64, p->d_twiddle, p->d_gen_pole,
                     p->d_gen_tau, p->d_gen_na, p->d_gen_z, p->d_gen_sin, p->tc.images, p->d_stage,
-                    p->d_whi, p->d_wlo, p->d_xthi, p->d_xtlo};
+                    p->d_whi, p->d_wlo, p->d_xthi, p->d_xtlo, p->d_nfst_kind, p->d_nfst_rows,
+                    p->d_nfst_znd};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     free_hier(p->hier);
@@ -424,7 +425,8 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
             if (hier_shape(n) && n >= kHierAutoMin) m = DCTPLUS_CAUCHY_HIER;
             else m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
         }
-        if ((m == DCTPLUS_CAUCHY_DENSE && !gemm_shape) ||
+        if ((m == DCTPLUS_CAUCHY_NFST && n > kF64Max) ||
+            (m == DCTPLUS_CAUCHY_DENSE && !gemm_shape) ||
             (m == DCTPLUS_CAUCHY_DENSE_GFT && !gemm_shape) ||
             (m == DCTPLUS_CAUCHY_HIER && !hier_shape(n)))
             return DCTPLUS_ERR_UNSUPPORTED;
@@ -507,6 +509,7 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
     if (n <= kSmallMax) st = setup_small_tc(p);
     else st = setup_large(p);
     if (st != DCTPLUS_OK) return st;
+    if (p->cauchy_mode == DCTPLUS_CAUCHY_NFST && (st = setup_nfst(p)) != DCTPLUS_OK) return st;
     DCTPLUS_CUDA_TRY(cudaDeviceSynchronize());
     return DCTPLUS_OK;
 }

@@ -1,0 +1,79 @@
+"""The paper's trigonometric route on the GPU (cauchy mode DCTPLUS_CAUCHY_NFST) against the
+oracle's version of the same route and the Cauchy-formula oracle."""
+import numpy as np
+import pytest
+import scipy.fft
+
+from oracle import cauchy, nfst_route
+from synthetic import edge_update_v, normal_signals, random_unit_v, self_loop_v
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_08970_gb300 as p
+    from paper_2409_08970_gb300 import build
+    build.build()
+    return p
+
+
+def conditioning(op):
+    mu = op.mu
+    inside = (mu > 0) & (mu < 4)
+    th = 2 * np.arctan2(np.sqrt(mu[inside]), np.sqrt(4 - mu[inside]))
+    return np.abs(np.sin(op.n * th)).min() if inside.any() else 1.0
+
+
+@pytest.mark.parametrize("n", [8, 16, 64, 100, 256, 1024])
+def test_route_matches_oracles(pkg, n):
+    cases = [(random_unit_v(n, seed=7), 0.7), (random_unit_v(n, seed=8), -0.3), (self_loop_v(n, 0), 2.0)]
+    if n >= 16:
+        cases.append((edge_update_v(n, n // 2 - 1, n // 2), -0.5))
+    for v, rho in cases:
+        op = cauchy.make_plan(n, v, rho)
+        x = normal_signals(50, n, seed=n)
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_NFST)
+        assert plan.cauchy_mode == pkg.CAUCHY_NFST
+        y = plan.forward(torch.tensor(x, dtype=torch.float64, device="cuda")).cpu().numpy()
+        same = nfst_route.transform(op, x)
+        ref = cauchy.transform(op, x)
+        tol = max(1e-12, 1e-13 * n / conditioning(op))
+        e_same = np.linalg.norm(y - same, axis=1) / np.linalg.norm(same, axis=1)
+        e_ref = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert e_same.max() < tol, (n, rho, e_same.max(), tol)
+        assert e_ref.max() < 2 * tol, (n, rho, e_ref.max(), tol)
+        y32 = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+        assert (np.linalg.norm(y32 - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() < 1e-6
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
+
+
+def test_route_conditioning_next_to_a_pole(pkg):
+    """A tiny weight z_10 puts a root next to pole 10: the route loses digits there, the
+    pole + offset form of the other modes does not."""
+    n = 64
+    z = np.random.default_rng(2).standard_normal(n)
+    z[10] = 1e-5
+    v = scipy.fft.idct(z, norm="ortho")
+    v /= np.linalg.norm(v)
+    op = cauchy.make_plan(n, v, 1.0)
+    x = normal_signals(20, n, seed=1)
+    ref = cauchy.transform(op, x)
+    route = pkg.Plan(n, v, 1.0, cauchy_mode=pkg.CAUCHY_NFST)
+    simt = pkg.Plan(n, v, 1.0, cauchy_mode=pkg.CAUCHY_SIMT)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    e_route = np.abs(route.forward(xd).cpu().numpy() - ref).max()
+    e_cauchy = np.abs(simt.forward(xd).cpu().numpy() - ref).max()
+    assert e_route > 1e3 * e_cauchy and e_cauchy < 1e-12
+    route.close()
+    simt.close()
+
+
+def test_route_size_limit(pkg):
+    with pytest.raises(pkg.DctPlusError) as e:
+        pkg.Plan(2048, self_loop_v(2048, 0), 1.0, cauchy_mode=pkg.CAUCHY_NFST)
+    assert e.value.status == 2
