@@ -23,16 +23,24 @@
 // (a stage is held from its TMA load until the DCT GEMM has read it, so the
 // ring depth bounds the loads in flight); all A-side operands the epilogue
 // forms live in TMEM.
-// Roles (480 threads, one persistent CTA per SM):
+// Roles (512 threads, one persistent CTA per SM):
 //   warp 0       TMA producer: x tiles into a 4-stage ring (128-byte swizzle)
-//   warp 1       TMEM owner and MMA issuer (one thread)
+//   warp 1       TMEM owner; one thread issues the DCT GEMMs and loads the
+//                plans' operand images
+//   warp 15      one thread issues the Cauchy GEMMs
 //   warps 2..9   x_lo and S_lo into TMEM; two warps per TMEM lane quarter,
 //                32 columns each
-//   warps 10..13 Y (TMEM) into registers and straight to global memory (a
-//                staging copy in shared memory would compete with the MMA
-//                operand reads for shared-memory bandwidth)
+//   warps 10..13 Y (TMEM) through registers into a shared-memory staging
+//                tile (128-byte swizzle), written out by TMA. Stores of rows
+//                straight from registers would touch 32 rows per instruction:
+//                their many small L2 writes queue in the load/store unit ahead
+//                of the shared-memory loads of the x_lo and S_lo warps.
 //   warp 14      the < 64/n signals of each segment that do not fill a packed
 //                row, on CUDA cores from the plan's FP32 tables
+// The two GEMM streams are issued from two threads, so that one thread's
+// barrier waits do not leave the tensor pipe idle while the other has work;
+// each thread's commits track only its own MMAs, and every buffer two GEMMs
+// share is handed over through an mbarrier.
 // TMEM columns: D1[3] 0..191, D2 192..255, S_lo[2] 256..383, x_lo[2] 384..511.
 // (The Y accumulator D2 is single buffered: its reader drains it right after
 // each Cauchy GEMM; S_lo and x_lo are double buffered so that neither GEMM
@@ -53,7 +61,7 @@ namespace dctplus {
 constexpr int kTcMaxSeg = 40;
 constexpr int kTcRows = 128;
 constexpr int kStages = 4;
-constexpr int kTcThreads = 480;
+constexpr int kTcThreads = 512;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 // shared-memory map (offsets from a 1024-byte aligned base)
@@ -61,7 +69,8 @@ constexpr uint32_t kImgBytes = 16384;               // one 64x64 TF32 operand im
 constexpr uint32_t kTileBytes = kTcRows * 64 * 4;   // 32 KB
 constexpr uint32_t kOffB = 0;                       // B1 hi, B1 lo, B2 hi, B2 lo
 constexpr uint32_t kOffX = 4 * kImgBytes;           // kStages x 32 KB
-constexpr uint32_t kOffBar = kOffX + kStages * kTileBytes;
+constexpr uint32_t kOffY = kOffX + kStages * kTileBytes;  // Y staging tile
+constexpr uint32_t kOffBar = kOffY + kTileBytes;
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;  // + barriers + alignment slack
 
 // TMEM column map
@@ -81,6 +90,7 @@ struct TcSeg {
 
 struct TcParams {
     CUtensorMap xmap[kTcMaxSeg];
+    CUtensorMap ymap[kTcMaxSeg];
     const float* images[kTcMaxSeg];  // 4 operand images of the segment's plan (64 KB)
     TcSeg seg[kTcMaxSeg];
     int nseg;
@@ -123,6 +133,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* Bimg = sm + kOffB;
     unsigned char* xbuf = sm + kOffX;
+    unsigned char* ybuf = sm + kOffY;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
     uint64_t* x_full = bars + 0;                // [kStages]
     uint64_t* x_empty = bars + kStages;         // [kStages]
@@ -133,9 +144,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
     uint64_t* d2_full = xlo_full + 2;           // Cauchy GEMM of the tile in D2 done
     uint64_t* d2_empty = d2_full + 1;           // D2 read out
     uint64_t* b_full = d2_empty + 1;
-    uint64_t* drain = b_full + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-    static_assert(8 * (2 * kStages + 15) <= 256, "barrier block");
+    uint64_t* drain = b_full + 1;               // DCT GEMM issuer's own MMAs done
+    uint64_t* drain2 = drain + 1;               // Cauchy GEMM issuer's own MMAs done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain2 + 1);
+    static_assert(8 * (2 * kStages + 16) <= 256, "barrier block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -162,6 +174,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         ptx::mbar_init(d2_empty, 4);
         ptx::mbar_init(b_full, 1);
         ptx::mbar_init(drain, 1);
+        ptx::mbar_init(drain2, 1);
         ptx::fence_mbar_init();
     }
     if (warp == 1) {
@@ -196,96 +209,89 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
                     ptx::mbar_wait(&x_full[i % kStages], (i / kStages) & 1, kWaitLimit);
             }
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
+    } else if (warp == 1 || warp == 15) {
+        // ---------------------------------------------------------- MMA issuers
         if (lane == 0) {
             constexpr uint32_t idesc = ptx::idesc_tf32(128, 64);
             // descriptors of the operand bases; a K step or another stage or
             // image only moves the start address (field in 16-byte units)
             const uint64_t dB0 = ptx::desc_sw128(ptx::smem_u32(Bimg));
-            const uint64_t dX0 = ptx::desc_sw128(ptx::smem_u32(xbuf));
             // K step k = 8 TF32 = 32 bytes inside a 128-byte swizzle row; K
             // block k / 4 is the next 128 (A tile) or 64 (B image) rows
-            auto kA16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kTileBytes / 32) + (k & 3) * 2); };
             auto kB16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kImgBytes / 32) + (k & 3) * 2); };
-            const float* cur = nullptr;
-            uint32_t nb = 0, nd = 0;
-            SegCursor cursor(P, t0);
-
-            // make the operand images of tile i's plan resident (drains the tensor pipe first)
-            auto ensure_plan = [&](int i) -> bool {
-                const float* img = P.images[cursor.at(P, t0 + i)];
-                if (img == cur) return true;
-                if (cur) {
-                    ptx::mma_commit(drain);
-                    if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) return false;
-                    ++nd;
+            if (warp == 1) {
+                // DCT GEMMs, S = X B1^T, corrections first and hi*hi last
+                const uint64_t dX0 = ptx::desc_sw128(ptx::smem_u32(xbuf));
+                auto kA16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kTileBytes / 32) + (k & 3) * 2); };
+                const float* cur = nullptr;
+                uint32_t nb = 0, nd = 0;
+                SegCursor cursor(P, t0);
+                for (int i = 0; i < count && ok; ++i) {
+                    const float* img = P.images[cursor.at(P, t0 + i)];
+                    if (img != cur) {
+                        // the old images are free once this thread's MMAs and the
+                        // Cauchy GEMM of tile i - 1 are done
+                        if (cur) {
+                            ptx::mma_commit(drain);
+                            if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) { ok = false; break; }
+                            ++nd;
+                            if (!ptx::mbar_wait(&d1_free[(i - 1) % 3], ((i - 1) / 3) & 1, kWaitLimit)) { ok = false; break; }
+                        }
+                        ptx::mbar_expect_tx(b_full, 4 * kImgBytes);
+                        ptx::bulk_load(Bimg, img, 4 * kImgBytes, b_full);
+                        if (!ptx::mbar_wait(b_full, nb & 1, kWaitLimit)) { ok = false; break; }
+                        ++nb;
+                        cur = img;
+                    }
+                    const int st = i % kStages, d = i % 3;
+                    // D1[d] was the hi operand of the Cauchy GEMM of tile i - 3
+                    if (i >= 3 && !ptx::mbar_wait(&d1_free[d], ((i / 3) - 1) & 1, kWaitLimit)) { ok = false; break; }
+                    if (!ptx::mbar_wait(&xlo_full[i & 1], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t d1 = tmem + kColD1 + d * 64;
+                    const uint64_t dA = dX0 + (uint64_t)(st * (kTileBytes >> 4));
+                    const uint32_t xl = tmem + kColXlo + (i & 1) * 64;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        ptx::mma_tf32(d1, dA + kA16(k), dB0 + 1 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        ptx::mma_tf32_ts(d1, xl + 8 * k, dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        ptx::mma_tf32(d1, dA + kA16(k), dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
+                    ptx::mma_commit(&x_empty[st]);
+                    ptx::mma_commit(&d1_full[d]);
                 }
-                ptx::mbar_expect_tx(b_full, 4 * kImgBytes);
-                ptx::bulk_load(Bimg, img, 4 * kImgBytes, b_full);
-                if (!ptx::mbar_wait(b_full, nb & 1, kWaitLimit)) return false;
-                ++nb;
-                cur = img;
-                return true;
-            };
-            // S = X B1^T for tile i: corrections first, hi*hi last
-            auto mma1 = [&](int i) -> bool {
-                const int s = i % kStages, d = i % 3;
-                // D1[d] was the hi operand of the Cauchy GEMM of tile i - 3
-                if (i >= 3 && !ptx::mbar_wait(&d1_free[d], ((i / 3) - 1) & 1, kWaitLimit)) return false;
-                if (!ptx::mbar_wait(&xlo_full[i & 1], (i >> 1) & 1, kWaitLimit)) return false;
-                ptx::tc_fence_after();
-                const uint32_t d1 = tmem + kColD1 + d * 64;
-                const uint64_t dA = dX0 + (uint64_t)(s * (kTileBytes >> 4));
-                const uint32_t xl = tmem + kColXlo + (i & 1) * 64;
+                // every MMA of this thread done before TMEM is released
+                ptx::mma_commit(drain);
+                if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) ok = false;
+            } else {
+                // Cauchy GEMMs, Y = S B2^T: S hi straight from the D1 accumulator,
+                // S_lo from TMEM. The images of tile i's plan are resident: they
+                // were loaded before its DCT GEMM, which S_lo (s_full) follows.
+                for (int i = 0; i < count && ok; ++i) {
+                    const int bf = i & 1;
+                    if (!ptx::mbar_wait(&s_full[bf], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
+                    if (!ptx::mbar_wait(d2_empty, (i & 1) ^ 1, kWaitLimit)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t d2 = tmem + kColD2;
+                    const uint32_t sh = tmem + kColD1 + (i % 3) * 64, sl = tmem + kColSlo + bf * 64;
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    ptx::mma_tf32(d1, dA + kA16(k), dB0 + 1 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
+                    for (int k = 0; k < 8; ++k)
+                        ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 3 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    ptx::mma_tf32_ts(d1, xl + 8 * k, dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
+                    for (int k = 0; k < 8; ++k)
+                        ptx::mma_tf32_ts(d2, sl + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    ptx::mma_tf32(d1, dA + kA16(k), dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
-                ptx::mma_commit(&x_empty[s]);
-                ptx::mma_commit(&d1_full[d]);
-                return true;
-            };
-            // Y = S B2^T for tile i: S hi straight from the D1 accumulator, S_lo from TMEM
-            auto mma2 = [&](int i) -> bool {
-                const int b = i & 1;
-                if (!ptx::mbar_wait(&s_full[b], (i >> 1) & 1, kWaitLimit)) return false;
-                if (!ptx::mbar_wait(d2_empty, (i & 1) ^ 1, kWaitLimit)) return false;
-                ptx::tc_fence_after();
-                const uint32_t d2 = tmem + kColD2;
-                const uint32_t sh = tmem + kColD1 + (i % 3) * 64, sl = tmem + kColSlo + b * 64;
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 3 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    ptx::mma_tf32_ts(d2, sl + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
-                ptx::mma_commit(d2_full);
-                ptx::mma_commit(&d1_free[i % 3]);
-                return true;
-            };
-
-            if (count > 0) ok = ensure_plan(0) && mma1(0);
-            for (int i = 0; i < count && ok; ++i) {
-                if (i + 1 < count) {
-                    const bool same = P.images[cursor.at(P, t0 + i + 1)] == cur;
-                    if (same) ok = mma1(i + 1) && mma2(i);
-                    else ok = mma2(i) && ensure_plan(i + 1) && mma1(i + 1);
-                } else {
-                    ok = mma2(i);
+                    for (int k = 0; k < 8; ++k)
+                        ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
+                    ptx::mma_commit(d2_full);
+                    ptx::mma_commit(&d1_free[i % 3]);
                 }
+                ptx::mma_commit(drain2);
+                if (!ptx::mbar_wait(drain2, 0, kWaitLimit)) ok = false;
             }
-            // every MMA done before TMEM is released
-            ptx::mma_commit(drain);
-            if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) ok = false;
             if (!ok) atomicOr(P.err, kErrTimeout);
         }
     } else if (warp < 10) {
@@ -332,8 +338,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             ptx::tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 32; ++j) u[j] = lo_tf32(__uint_as_float(u[j]));
-            // S_lo[i & 1] was read by the Cauchy GEMM of tile i - 2, which was
-            // issued before the DCT GEMM of tile i: d1_full covers it
+            // S_lo[i & 1] was read by the Cauchy GEMM of tile i - 2 (issued by
+            // the other thread, so d1_full does not cover it)
+            if (i >= 2 && !ptx::mbar_wait(&d1_free[(i - 2) % 3], ((i - 2) / 3) & 1, kWaitLimit)) { ok = false; break; }
+            ptx::tc_fence_after();
             const uint32_t scol = tmem + lanes + kColSlo + (i & 1) * 64 + 32 * h;
             ptx::tmem_st16(scol, *reinterpret_cast<uint32_t(*)[16]>(u));
             ptx::tmem_st16(scol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
@@ -348,31 +356,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         const int q = warp & 3;
         const int r = 32 * q + lane;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        const int gtid = threadIdx.x - 320;     // 0..127
         uint32_t u[64];
         SegCursor cursor(P, t0);
         for (int i = 0; i < count && ok; ++i) {
             const int tile = t0 + i;
             const int sg = cursor.at(P, tile);
             const int row0 = (tile - P.seg[sg].tile_start) * kTcRows;
-            if (!ptx::mbar_wait(d2_full, i & 1, kWaitLimit)) { ok = false; break; }
-            ptx::tc_fence_after();
+            // every Y thread reaches both named barriers of the iteration; a
+            // wait that ran out ends the loop for all four warps together
+            const bool got = __all_sync(0xffffffffu, ptx::mbar_wait(d2_full, i & 1, kWaitLimit));
+            if (got) {
+                ptx::tc_fence_after();
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                ptx::tmem_ld16(tmem + lanes + kColD2 + 16 * j, *reinterpret_cast<uint32_t(*)[16]>(u + 16 * j));
-            ptx::tmem_wait_ld();
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(d2_empty);
-            // row r of the tile straight from registers to global memory (no shared-memory
-            // staging, which would compete with the MMA operand reads)
-            if (row0 + r < P.seg[sg].rows64) {
-                float4* dst = reinterpret_cast<float4*>(P.seg[sg].y + (int64_t)(row0 + r) * 64);
+                for (int j = 0; j < 4; ++j)
+                    ptx::tmem_ld16(tmem + lanes + kColD2 + 16 * j, *reinterpret_cast<uint32_t(*)[16]>(u + 16 * j));
+                ptx::tmem_wait_ld();
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(d2_empty);
+            }
+            // the previous tile's store has read the staging tile
+            if (gtid == 0) ptx::bulk_wait_group_read0();
+            if (!ptx::named_bar_and(2, 128, got)) { ok = false; break; }
 #pragma unroll
-                for (int cc = 0; cc < 16; ++cc)
-                    __stcs(dst + cc, make_float4(__uint_as_float(u[4 * cc]), __uint_as_float(u[4 * cc + 1]),
-                                                 __uint_as_float(u[4 * cc + 2]), __uint_as_float(u[4 * cc + 3])));
+            for (int cc = 0; cc < 16; ++cc)
+                *reinterpret_cast<uint4*>(ybuf + sw128_off(r, cc)) =
+                    make_uint4(u[4 * cc], u[4 * cc + 1], u[4 * cc + 2], u[4 * cc + 3]);
+            ptx::fence_proxy_async_smem();
+            ptx::named_bar_sync(2, 128);
+            if (gtid == 0) {
+                // rows past the segment's end are clipped by the tensor map
+                ptx::tma_store_2d(&P.ymap[sg], 0, row0, ybuf);
+                ptx::tma_store_2d(&P.ymap[sg], 32, row0, ybuf + kTileBytes / 2);
+                ptx::bulk_commit_group();
             }
         }
+        if (gtid == 0) ptx::bulk_wait_group0();
         if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
     } else {
         // ------------------------------------------- leftover signals (warp 14)
@@ -507,7 +527,7 @@ dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream
             const int64_t rows64 = g.rows * n / 64;
             const int64_t body = rows64 * 64 / n;
             if (g.rows <= 0) continue;
-            if (rows64 > 0 && (!encode_map(&P.xmap[ns], g.x, rows64)))
+            if (rows64 > 0 && (!encode_map(&P.xmap[ns], g.x, rows64) || !encode_map(&P.ymap[ns], g.y, rows64)))
                 return DCTPLUS_ERR_CUDA;
             P.images[ns] = g.plan->tc.images;
             TcSeg& t = P.seg[ns];
