@@ -26,8 +26,8 @@
 // Roles (512 threads, one persistent CTA per SM):
 //   warp 0       TMA producer: x tiles into a 4-stage ring (128-byte swizzle)
 //   warp 1       TMEM owner; one thread issues the DCT GEMMs and loads the
-//                plans' operand images
-//   warp 15      one thread issues the Cauchy GEMMs
+//                DCT operand images (they depend on n only)
+//   warp 15      one thread issues the Cauchy GEMMs and loads the W images
 //   warps 2..9   x_lo and S_lo into TMEM; two warps per TMEM lane quarter,
 //                32 columns each
 //   warps 10..13 Y (TMEM) through registers into a shared-memory staging
@@ -40,7 +40,10 @@
 // The two GEMM streams are issued from two threads, so that one thread's
 // barrier waits do not leave the tensor pipe idle while the other has work;
 // each thread's commits track only its own MMAs, and every buffer two GEMMs
-// share is handed over through an mbarrier.
+// share is handed over through an mbarrier. At a segment boundary each
+// thread drains only its own GEMMs before replacing its half of the operand
+// images (the DCT half only when n changes), so the other GEMM stream keeps
+// the tensor pipe busy during the reload.
 // TMEM columns: D1[3] 0..191, D2 192..255, S_lo[2] 256..383, x_lo[2] 384..511.
 // (The Y accumulator D2 is single buffered: its reader drains it right after
 // each Cauchy GEMM; S_lo and x_lo are double buffered so that neither GEMM
@@ -146,8 +149,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
     uint64_t* b_full = d2_empty + 1;
     uint64_t* drain = b_full + 1;               // DCT GEMM issuer's own MMAs done
     uint64_t* drain2 = drain + 1;               // Cauchy GEMM issuer's own MMAs done
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain2 + 1);
-    static_assert(8 * (2 * kStages + 16) <= 256, "barrier block");
+    uint64_t* b2_full = drain2 + 1;             // W images loaded
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b2_full + 1);
+    static_assert(8 * (2 * kStages + 17) <= 256, "barrier block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         ptx::mbar_init(b_full, 1);
         ptx::mbar_init(drain, 1);
         ptx::mbar_init(drain2, 1);
+        ptx::mbar_init(b2_full, 1);
         ptx::fence_mbar_init();
     }
     if (warp == 1) {
@@ -223,25 +228,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
                 // DCT GEMMs, S = X B1^T, corrections first and hi*hi last
                 const uint64_t dX0 = ptx::desc_sw128(ptx::smem_u32(xbuf));
                 auto kA16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kTileBytes / 32) + (k & 3) * 2); };
-                const float* cur = nullptr;
+                int cur_n = 0;
                 uint32_t nb = 0, nd = 0;
                 SegCursor cursor(P, t0);
                 for (int i = 0; i < count && ok; ++i) {
-                    const float* img = P.images[cursor.at(P, t0 + i)];
-                    if (img != cur) {
-                        // the old images are free once this thread's MMAs and the
-                        // Cauchy GEMM of tile i - 1 are done
-                        if (cur) {
+                    const int sg = cursor.at(P, t0 + i);
+                    if (P.seg[sg].n != cur_n) {
+                        // B1 = I (x) U^T depends on n only; the old one is free once
+                        // this thread's own MMAs are done
+                        if (cur_n) {
                             ptx::mma_commit(drain);
                             if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) { ok = false; break; }
                             ++nd;
-                            if (!ptx::mbar_wait(&d1_free[(i - 1) % 3], ((i - 1) / 3) & 1, kWaitLimit)) { ok = false; break; }
                         }
-                        ptx::mbar_expect_tx(b_full, 4 * kImgBytes);
-                        ptx::bulk_load(Bimg, img, 4 * kImgBytes, b_full);
+                        ptx::mbar_expect_tx(b_full, 2 * kImgBytes);
+                        ptx::bulk_load(Bimg, P.images[sg], 2 * kImgBytes, b_full);
                         if (!ptx::mbar_wait(b_full, nb & 1, kWaitLimit)) { ok = false; break; }
                         ++nb;
-                        cur = img;
+                        cur_n = P.seg[sg].n;
                     }
                     const int st = i % kStages, d = i % 3;
                     // D1[d] was the hi operand of the Cauchy GEMM of tile i - 3
@@ -268,12 +272,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
                 if (!ptx::mbar_wait(drain, nd & 1, kWaitLimit)) ok = false;
             } else {
                 // Cauchy GEMMs, Y = S B2^T: S hi straight from the D1 accumulator,
-                // S_lo from TMEM. The images of tile i's plan are resident: they
-                // were loaded before its DCT GEMM, which S_lo (s_full) follows.
+                // S_lo from TMEM
+                const float* cur = nullptr;
+                uint32_t nb2 = 0, nd2 = 0;
+                bool pending = false;  // a W image copy not yet waited for
+                SegCursor cursor(P, t0);
                 for (int i = 0; i < count && ok; ++i) {
                     const int bf = i & 1;
+                    const float* img = P.images[cursor.at(P, t0 + i)];
+                    const bool load = img != cur;
+                    if (load) {
+                        // the old W images are free once this thread's own MMAs are done;
+                        // the copy overlaps the wait for tile i's S_lo
+                        if (cur) {
+                            ptx::mma_commit(drain2);
+                            if (!ptx::mbar_wait(drain2, nd2 & 1, kWaitLimit)) { ok = false; break; }
+                            ++nd2;
+                        }
+                        ptx::mbar_expect_tx(b2_full, 2 * kImgBytes);
+                        ptx::bulk_load(Bimg + 2 * kImgBytes, img + 2 * (kImgBytes / 4), 2 * kImgBytes, b2_full);
+                        pending = true;
+                        cur = img;
+                    }
                     if (!ptx::mbar_wait(&s_full[bf], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
                     if (!ptx::mbar_wait(d2_empty, (i & 1) ^ 1, kWaitLimit)) { ok = false; break; }
+                    if (load) {
+                        if (!ptx::mbar_wait(b2_full, nb2 & 1, kWaitLimit)) { ok = false; break; }
+                        ++nb2;
+                        pending = false;
+                    }
                     ptx::tc_fence_after();
                     const uint32_t d2 = tmem + kColD2;
                     const uint32_t sh = tmem + kColD1 + (i % 3) * 64, sl = tmem + kColSlo + bf * 64;
@@ -289,8 +316,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
                     ptx::mma_commit(d2_full);
                     ptx::mma_commit(&d1_free[i % 3]);
                 }
+                // a copy still in flight after a failed wait lands before the CTA exits
+                if (pending) ptx::mbar_wait(b2_full, nb2 & 1, kWaitLimit);
                 ptx::mma_commit(drain2);
-                if (!ptx::mbar_wait(drain2, 0, kWaitLimit)) ok = false;
+                if (!ptx::mbar_wait(drain2, nd2 & 1, kWaitLimit)) ok = false;
             }
             if (!ok) atomicOr(P.err, kErrTimeout);
         }
