@@ -11,14 +11,19 @@
 // hi + lo with hi, lo TF32, and a product takes hi*hi + hi*lo + lo*hi,
 // accumulated in FP32 in tensor memory (TMEM). For x and S the hi part is the
 // FP32 value itself, which the MMA reads truncated to TF32 (S straight from
-// its TMEM accumulator), and lo = rn_tf32(v - trunc_tf32(v)); for the plan's
-// matrices hi and lo are both rounded. The MMA accumulates like
-// round-toward-zero, so the two small correction products are issued first
-// and the hi*hi terms last: the large partial sums see 8 roundings, not 24.
+// TMEM), and lo = rn_tf32(v - trunc_tf32(v)); for the plan's matrices hi and
+// lo are both rounded. The plan's hi and lo are stacked into one 128-row B
+// operand, so hi*[B_hi; B_lo] is a single N = 128 MMA per K step (an N = 64
+// MMA runs at about half the rate of an N = 128 one): it writes the main
+// term hi*B_hi into columns 0..63 of a 128-column accumulator and hi*B_lo
+// into columns 64..127, where the N = 64 MMA lo*B_hi then accumulates. The
+// two halves are added in FP32 (round to nearest) by the warps that read
+// them: for S by the S_lo warps, which write S and S_lo back in place, for Y
+// by the Y warps.
 //
-// Pipeline: the DCT GEMM of tile t+1 is issued before the Cauchy GEMM of tile
-// t, so it runs while the epilogue forms tile t's S_lo; x_lo is double
-// buffered, so x_lo of tile t+1 is formed while the DCT GEMM of tile t runs.
+// Pipeline: x_lo is double buffered, so x_lo of tile t+1 is formed while the
+// DCT GEMM of tile t runs, and so is the DCT accumulator (which then holds S
+// and S_lo), so the DCT GEMM of tile t+1 runs while tile t's S is split.
 // Shared memory holds the plan's operand images and a 4-stage ring of x tiles
 // (a stage is held from its TMA load until the DCT GEMM has read it, so the
 // ring depth bounds the loads in flight); all A-side operands the epilogue
@@ -44,10 +49,9 @@
 // thread drains only its own GEMMs before replacing its half of the operand
 // images (the DCT half only when n changes), so the other GEMM stream keeps
 // the tensor pipe busy during the reload.
-// TMEM columns: D1[3] 0..191, D2 192..255, S_lo[2] 256..383, x_lo[2] 384..511.
-// (The Y accumulator D2 is single buffered: its reader drains it right after
-// each Cauchy GEMM; S_lo and x_lo are double buffered so that neither GEMM
-// waits on the other's previous tile.)
+// TMEM columns: D1[2] 0..255 (128 each: S | S_lo after the split), D2 256..383,
+// x_lo[2] 384..511. (The Y accumulator D2 is single buffered: its reader
+// drains it right after each Cauchy GEMM.)
 // Every mbarrier wait is bounded; a wait that runs out sets the device error
 // word and the CTA winds down (no trap, TMEM released).
 #include <cudaTypedefs.h>
@@ -68,16 +72,16 @@ constexpr int kTcThreads = 512;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 // shared-memory map (offsets from a 1024-byte aligned base)
-constexpr uint32_t kImgBytes = 16384;               // one 64x64 TF32 operand image
+constexpr uint32_t kImgBytes = 16384;               // one 64x64 TF32 operand (hi or lo)
 constexpr uint32_t kTileBytes = kTcRows * 64 * 4;   // 32 KB
-constexpr uint32_t kOffB = 0;                       // B1 hi, B1 lo, B2 hi, B2 lo
+constexpr uint32_t kOffB = 0;                       // [B1 hi; B1 lo], [B2 hi; B2 lo]
 constexpr uint32_t kOffX = 4 * kImgBytes;           // kStages x 32 KB
 constexpr uint32_t kOffY = kOffX + kStages * kTileBytes;  // Y staging tile
 constexpr uint32_t kOffBar = kOffY + kTileBytes;
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;  // + barriers + alignment slack
 
 // TMEM column map
-constexpr uint32_t kColD1 = 0, kColD2 = 192, kColSlo = 256, kColXlo = 384;
+constexpr uint32_t kColD1 = 0, kColD2 = 256, kColXlo = 384;
 
 struct TcSeg {
     int tile_start;     // first tile index of the segment in this launch
@@ -94,7 +98,7 @@ struct TcSeg {
 struct TcParams {
     CUtensorMap xmap[kTcMaxSeg];
     CUtensorMap ymap[kTcMaxSeg];
-    const float* images[kTcMaxSeg];  // 4 operand images of the segment's plan (64 KB)
+    const float* images[kTcMaxSeg];  // the segment's plan's operand images (64 KB)
     TcSeg seg[kTcMaxSeg];
     int nseg;
     int ntiles;
@@ -140,9 +144,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
     uint64_t* x_full = bars + 0;                // [kStages]
     uint64_t* x_empty = bars + kStages;         // [kStages]
-    uint64_t* d1_full = bars + 2 * kStages;     // [3] DCT GEMM of the tile in D1[d] done
-    uint64_t* d1_free = d1_full + 3;            // [3] Cauchy GEMM that read D1[d] done
-    uint64_t* s_full = d1_free + 3;             // [2] S_lo[b] written
+    uint64_t* d1_full = bars + 2 * kStages;     // [2] DCT GEMM of the tile in D1[d] done
+    uint64_t* d1_free = d1_full + 2;            // [2] Cauchy GEMM that read D1[d] done
+    uint64_t* s_full = d1_free + 2;             // [2] S and S_lo written into D1[d]
     uint64_t* xlo_full = s_full + 2;            // [2] x_lo[b] written
     uint64_t* d2_full = xlo_full + 2;           // Cauchy GEMM of the tile in D2 done
     uint64_t* d2_empty = d2_full + 1;           // D2 read out
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
     uint64_t* drain2 = drain + 1;               // Cauchy GEMM issuer's own MMAs done
     uint64_t* b2_full = drain2 + 1;             // W images loaded
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b2_full + 1);
-    static_assert(8 * (2 * kStages + 17) <= 256, "barrier block");
+    static_assert(8 * (2 * kStages + 15) <= 256, "barrier block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -166,11 +170,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             ptx::mbar_init(&x_full[i], 1);
             ptx::mbar_init(&x_empty[i], 1);
         }
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&d1_full[i], 1);
             ptx::mbar_init(&d1_free[i], 1);
-        }
-        for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&s_full[i], 8);
             ptx::mbar_init(&xlo_full[i], 8);
         }
@@ -217,17 +219,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
     } else if (warp == 1 || warp == 15) {
         // ---------------------------------------------------------- MMA issuers
         if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_tf32(128, 64);
+            constexpr uint32_t idesc64 = ptx::idesc_tf32(128, 64);
+            constexpr uint32_t idesc128 = ptx::idesc_tf32(128, 128);
             // descriptors of the operand bases; a K step or another stage or
-            // image only moves the start address (field in 16-byte units)
+            // matrix only moves the start address (field in 16-byte units)
             const uint64_t dB0 = ptx::desc_sw128(ptx::smem_u32(Bimg));
             // K step k = 8 TF32 = 32 bytes inside a 128-byte swizzle row; K
-            // block k / 4 is the next 128 (A tile) or 64 (B image) rows
-            auto kB16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kImgBytes / 32) + (k & 3) * 2); };
+            // block k / 4 is the next 128 rows (16 KB) of an A tile or a
+            // stacked [hi; lo] B operand, whose first 64 rows are hi
+            auto k16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kTileBytes / 32) + (k & 3) * 2); };
+            constexpr uint64_t kB2 = (2 * kImgBytes) >> 4;   // [B2 hi; B2 lo]
             if (warp == 1) {
                 // DCT GEMMs, S = X B1^T, corrections first and hi*hi last
                 const uint64_t dX0 = ptx::desc_sw128(ptx::smem_u32(xbuf));
-                auto kA16 = [](int k) -> uint64_t { return (uint64_t)((k >> 2) * (kTileBytes / 32) + (k & 3) * 2); };
                 int cur_n = 0;
                 uint32_t nb = 0, nd = 0;
                 SegCursor cursor(P, t0);
@@ -247,23 +251,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
                         ++nb;
                         cur_n = P.seg[sg].n;
                     }
-                    const int st = i % kStages, d = i % 3;
-                    // D1[d] was the hi operand of the Cauchy GEMM of tile i - 3
-                    if (i >= 3 && !ptx::mbar_wait(&d1_free[d], ((i / 3) - 1) & 1, kWaitLimit)) { ok = false; break; }
+                    const int st = i % kStages, d = i & 1;
+                    // D1[d] held S and S_lo of tile i - 2 for its Cauchy GEMM
+                    if (i >= 2 && !ptx::mbar_wait(&d1_free[d], ((i >> 1) - 1) & 1, kWaitLimit)) { ok = false; break; }
                     if (!ptx::mbar_wait(&xlo_full[i & 1], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
                     ptx::tc_fence_after();
-                    const uint32_t d1 = tmem + kColD1 + d * 64;
+                    const uint32_t d1 = tmem + kColD1 + d * 128;
                     const uint64_t dA = dX0 + (uint64_t)(st * (kTileBytes >> 4));
                     const uint32_t xl = tmem + kColXlo + (i & 1) * 64;
+                    // x_hi [B1 hi; B1 lo]^T into both halves, then x_lo B1_hi^T into the second
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
-                        ptx::mma_tf32(d1, dA + kA16(k), dB0 + 1 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
+                        ptx::mma_tf32(d1, dA + k16(k), dB0 + k16(k), idesc128, k > 0);
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
-                        ptx::mma_tf32_ts(d1, xl + 8 * k, dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        ptx::mma_tf32(d1, dA + kA16(k), dB0 + 0 * (kImgBytes >> 4) + kB16(k), idesc, 1);
+                        ptx::mma_tf32_ts(d1 + 64, xl + 8 * k, dB0 + k16(k), idesc64, 1);
                     ptx::mma_commit(&x_empty[st]);
                     ptx::mma_commit(&d1_full[d]);
                 }
@@ -303,18 +305,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
                     }
                     ptx::tc_fence_after();
                     const uint32_t d2 = tmem + kColD2;
-                    const uint32_t sh = tmem + kColD1 + (i % 3) * 64, sl = tmem + kColSlo + bf * 64;
+                    const uint32_t sh = tmem + kColD1 + bf * 128, sl = sh + 64;
+                    // S [B2 hi; B2 lo]^T into both halves, then S_lo B2_hi^T into the second
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
-                        ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 3 * (kImgBytes >> 4) + kB16(k), idesc, k > 0);
+                        ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + kB2 + k16(k), idesc128, k > 0);
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
-                        ptx::mma_tf32_ts(d2, sl + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        ptx::mma_tf32_ts(d2, sh + 8 * k, dB0 + 2 * (kImgBytes >> 4) + kB16(k), idesc, 1);
+                        ptx::mma_tf32_ts(d2 + 64, sl + 8 * k, dB0 + kB2 + k16(k), idesc64, 1);
                     ptx::mma_commit(d2_full);
-                    ptx::mma_commit(&d1_free[i % 3]);
+                    ptx::mma_commit(&d1_free[bf]);
                 }
                 // a copy still in flight after a failed wait lands before the CTA exits
                 if (pending) ptx::mbar_wait(b2_full, nb2 & 1, kWaitLimit);
@@ -354,26 +354,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
         };
 
         if (count > 0) ok = conv(0);
+        uint32_t v[32];
         for (int i = 0; i < count && ok; ++i) {
-            const int d = i % 3;
+            const int d = i & 1;
             // x_lo buffer (i + 1) & 1 was read by the DCT GEMM of tile i - 1,
             // complete since the previous iteration waited on it
             if (i + 1 < count && !conv(i + 1)) { ok = false; break; }
-            if (!ptx::mbar_wait(&d1_full[d], (i / 3) & 1, kWaitLimit)) { ok = false; break; }
+            if (!ptx::mbar_wait(&d1_full[d], (i >> 1) & 1, kWaitLimit)) { ok = false; break; }
             ptx::tc_fence_after();
-            const uint32_t dcol = tmem + lanes + kColD1 + d * 64 + 32 * h;
-            ptx::tmem_ld16(dcol, *reinterpret_cast<uint32_t(*)[16]>(u));
-            ptx::tmem_ld16(dcol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
+            // S = main + correction half (round to nearest), then split it in place:
+            // S over the main half, S_lo over the correction half
+            const uint32_t mcol = tmem + lanes + kColD1 + d * 128 + 32 * h, ccol = mcol + 64;
+            ptx::tmem_ld16(mcol, *reinterpret_cast<uint32_t(*)[16]>(u));
+            ptx::tmem_ld16(mcol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
+            ptx::tmem_ld16(ccol, *reinterpret_cast<uint32_t(*)[16]>(v));
+            ptx::tmem_ld16(ccol + 16, *reinterpret_cast<uint32_t(*)[16]>(v + 16));
             ptx::tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) u[j] = lo_tf32(__uint_as_float(u[j]));
-            // S_lo[i & 1] was read by the Cauchy GEMM of tile i - 2 (issued by
-            // the other thread, so d1_full does not cover it)
-            if (i >= 2 && !ptx::mbar_wait(&d1_free[(i - 2) % 3], ((i - 2) / 3) & 1, kWaitLimit)) { ok = false; break; }
-            ptx::tc_fence_after();
-            const uint32_t scol = tmem + lanes + kColSlo + (i & 1) * 64 + 32 * h;
-            ptx::tmem_st16(scol, *reinterpret_cast<uint32_t(*)[16]>(u));
-            ptx::tmem_st16(scol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
+            for (int j = 0; j < 32; ++j) {
+                const float sv = __uint_as_float(u[j]) + __uint_as_float(v[j]);
+                u[j] = __float_as_uint(sv);
+                v[j] = lo_tf32(sv);
+            }
+            ptx::tmem_st16(mcol, *reinterpret_cast<uint32_t(*)[16]>(u));
+            ptx::tmem_st16(mcol + 16, *reinterpret_cast<uint32_t(*)[16]>(u + 16));
+            ptx::tmem_st16(ccol, *reinterpret_cast<uint32_t(*)[16]>(v));
+            ptx::tmem_st16(ccol + 16, *reinterpret_cast<uint32_t(*)[16]>(v + 16));
             ptx::tmem_wait_st();
             ptx::tc_fence_before();
             __syncwarp();
@@ -397,10 +403,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
             const bool got = __all_sync(0xffffffffu, ptx::mbar_wait(d2_full, i & 1, kWaitLimit));
             if (got) {
                 ptx::tc_fence_after();
+                // Y = main + correction half (round to nearest); the correction
+                // half comes in 8 columns at a time to bound the registers
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     ptx::tmem_ld16(tmem + lanes + kColD2 + 16 * j, *reinterpret_cast<uint32_t(*)[16]>(u + 16 * j));
-                ptx::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    uint32_t w[8];
+                    ptx::tmem_ld8(tmem + lanes + kColD2 + 64 + 8 * j, w);
+                    ptx::tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        u[8 * j + e] = __float_as_uint(__uint_as_float(u[8 * j + e]) + __uint_as_float(w[e]));
+                }
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(d2_empty);
@@ -458,9 +474,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_small_tc(const __grid_constan
 
 // --------------------------------------------------------- operand images
 
-// The four 64x64 B operands (N rows x K, K-major) of a plan, block diagonal
-// over 64/n copies: B1 = I (x) U^T, B2 = I (x) W; each split into TF32 hi and
-// lo, written in the 128-byte-swizzled layout the MMA reads from shared memory.
+// The two B operands of a plan, block diagonal over 64/n copies: B1 = I (x)
+// U^T, B2 = I (x) W, each split into TF32 hi and lo and stacked as one 128 x 64
+// operand [hi; lo] (N rows x K, K-major), in the 128-byte-swizzled layout the
+// MMA reads from shared memory: per matrix two K blocks of 128 rows x 128 B.
 __global__ void k_tc_images(int n, const double* ct64, const double* w64, float* img) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;  // r * 64 + k
     if (idx >= 64 * 64) return;
@@ -469,15 +486,16 @@ __global__ void k_tc_images(int n, const double* ct64, const double* w64, float*
     double b1 = same ? ct64[(r % n) * n + (k % n)] : 0.0;
     double b2 = same ? w64[(r % n) * n + (k % n)] : 0.0;
     int kb = k / 32, c = (k % 32) / 4, e = k % 4;
-    int off = (kb * 8192 + r * 128 + ((c ^ (r & 7)) << 4) + e * 4) / 4;  // in floats
+    // byte offset of (row R, k) inside one stacked operand; R = r (hi) or 64 + r (lo)
+    auto off = [&](int R) { return (kb * 16384 + R * 128 + ((c ^ (R & 7)) << 4) + e * 4) / 4; };
     float h1 = ptx::tf32_round((float)b1);
     float l1 = ptx::tf32_round((float)(b1 - (double)h1));
     float h2 = ptx::tf32_round((float)b2);
     float l2 = ptx::tf32_round((float)(b2 - (double)h2));
-    img[0 * 4096 + off] = h1;
-    img[1 * 4096 + off] = l1;
-    img[2 * 4096 + off] = h2;
-    img[3 * 4096 + off] = l2;
+    img[off(r)] = h1;
+    img[off(64 + r)] = l1;
+    img[8192 + off(r)] = h2;
+    img[8192 + off(64 + r)] = l2;
 }
 
 static bool tc_size(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
