@@ -68,7 +68,7 @@ typedef enum {
     DCTPLUS_CAUCHY_AUTO = 0,  /* pick by n */
     DCTPLUS_CAUCHY_DENSE = 1, /* dense split-TF32 tensor-core product with the plan's
                                  W = diag(a) C(mu, lambda) diag(z) table; n % 128 == 0, n <= 4096 */
-    DCTPLUS_CAUCHY_HIER = 2,  /* O(n log n) hierarchical far-field expansion (Theorem 3.2) */
+    DCTPLUS_CAUCHY_HIER = 2,  /* near-field band + leaf-level Chebyshev far field (Theorem 3.2's fast-product family) */
     DCTPLUS_CAUCHY_SIMT = 3,  /* CUDA-core product, W from a stored table (n <= 4096) or
                                  generated tile by tile in shared memory */
     DCTPLUS_CAUCHY_DENSE_GFT = 4, /* comparison baseline, not the factored method: one dense

@@ -16,16 +16,23 @@
 //               entries of W, a band matrix applied on the tensor cores with
 //               the split-TF32 GEMM (each 128-row output tile contracts a
 //               K window of s against a compact [n x Kw] slab of W entries);
-//   far field   every other source, through Chebyshev expansions of degree R:
-//               P2M at the leaves (z folded into the weights), M2M up the tree,
-//               M2L between well-separated boxes of each level, L2L down, L2P
-//               at the target leaves (-a folded into the weights); one CTA per
-//               group of up to 16 signals on CUDA cores, added into y.
+//   far field   every other source, through Chebyshev interpolation of degree
+//               R in both variables at the leaf level: P2M (per leaf, the
+//               sources' z-weighted interpolation coefficients, CUDA cores),
+//               then one dense product with the kernel sampled at the leaf
+//               nodes of every well-separated leaf pair (target leaf I,
+//               source leaf J, |I - J| >= 2), a [nleaf R x nleaf R] matrix on
+//               the tensor cores (split-TF32 GEMM), then L2P (-a folded into
+//               the weights, CUDA cores) added into y. A single level with a
+//               dense leaf-to-leaf operator trades the tree's O(n) M2L work for
+//               (12 n / 64)^2 tensor-core multiply-adds per signal, fewer than
+//               the dense product's n^2 by (64 / 12)^2.
 // Roots outside [0, 4] (at most the largest for rho > 0 or the smallest for
 // rho < 0; the paper's pre-processing isolates the same root) have no real
 // angle; their rows are dense dot products.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -37,24 +44,32 @@ constexpr int kLeaf = 64;
 constexpr int kR = 12;  // Chebyshev degree of the far-field expansions
 
 struct HierTables {
-    int nleaf = 0, L = 0, Kw = 0;
+    int nleaf = 0, Kw = 0;
+    int nc = 0, ncp = 0;         // leaf coefficients nleaf R, padded to a multiple of 128
     std::vector<int> kbeg;       // per 128-row output tile: first source of the K window
     float* slab_hi = nullptr;    // n x Kw
     float* slab_lo = nullptr;
     float* zf = nullptr;         // n: z_j (0 where deflated)
     float* tq = nullptr;         // 64 x R: S_a at the 64 source positions of any leaf
-    float* pu = nullptr;         // n: position of row r in its leaf, in [-1, 1]
     float* pna = nullptr;        // n: -a_r for far-field targets, 0 otherwise
     float* wl = nullptr;         // R x n: L2P weights -a_r S_a(u_r) (0 for other rows)
-    float* cheb = nullptr;       // 2 x R: Chebyshev nodes and barycentric weights
     int* row_leaf = nullptr;     // n
-    float* tlr = nullptr;        // 2 x R x R: parent basis at left / right child nodes
-    float* m2l = nullptr;        // (2^(L+1) - 1) x 3 x R x R
-    int* il = nullptr;           // (2^(L+1) - 1) x 3 interaction-list boxes (-1: none)
+    float* kf_hi = nullptr;      // ncp x ncp: leaf-to-leaf kernel samples, TF32 hi
+    float* kf_lo = nullptr;      //            and lo (zero for near pairs and padding)
     int nout = 0;
     int out_row[2] = {-1, -1};
     float* out_w = nullptr;      // nout x n dense rows
 };
+
+// round to TF32 (10 explicit mantissa bits), nearest-even; finite inputs
+static float tf32_host(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u = (u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
 
 // Lagrange basis polynomial a on the degree-R Chebyshev nodes of [-1, 1], at u
 static double cheb_lagrange(int a, double u) {
@@ -108,8 +123,8 @@ __global__ void k_band_slab(int n, int Kw, const int* kbeg_tile, const int* row_
 
 void free_hier(HierTables* h) {
     if (!h) return;
-    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf, h->tq, h->pu, h->pna, h->wl, h->cheb,
-                    h->row_leaf, h->tlr, h->m2l, h->il, h->out_w};
+    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf, h->tq, h->pna, h->wl, h->row_leaf,
+                    h->kf_hi, h->kf_lo, h->out_w};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
@@ -123,9 +138,7 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     HierTables* h = new HierTables();
     p->hier = h;
     h->nleaf = n / kLeaf;
-    h->L = 0;
-    while ((1 << h->L) < h->nleaf) ++h->L;
-    const int nleaf = h->nleaf, L = h->L;
+    const int nleaf = h->nleaf;
     const double hleaf = M_PI / nleaf;  // th-width of a leaf
 
     // z with deflated entries zero (host)
@@ -176,7 +189,7 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
 
     // P2M: every leaf holds 64 sources at the same relative positions, so the
     // weights are z_j S_a(u_jj) with one 64 x R table; L2P: per-row position and -a_r
-    std::vector<float> zf(n), tq((size_t)kLeaf * kR), pu(n, 0.0f), pna(n, 0.0f), cheb(2 * kR);
+    std::vector<float> zf(n), tq((size_t)kLeaf * kR), pna(n, 0.0f);
     for (int j = 0; j < n; ++j) zf[j] = (float)znd[j];
     for (int jj = 0; jj < kLeaf; ++jj) {
         double u = (jj + 0.0) / kLeaf * 2.0 - 1.0;  // th_j within its leaf, scaled to [-1, 1)
@@ -184,9 +197,6 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     }
     for (int r = 0; r < n; ++r) {
         if (row_leaf[r] < 0 || p->row_kind[r] == 0) continue;
-        int b = row_leaf[r];
-        double c = (b + 0.5) * hleaf, hw = 0.5 * hleaf;
-        pu[r] = (float)((ph[r] - c) / hw);
         pna[r] = (float)(-p->row_a[r]);
     }
     std::vector<float> wl((size_t)kR * n, 0.0f);
@@ -197,42 +207,29 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         for (int a = 0; a < kR; ++a)
             wl[(size_t)a * n + r] = (float)(-p->row_a[r] * cheb_lagrange(a, (ph[r] - c) / hw));
     }
-    for (int a = 0; a < kR; ++a) {
-        cheb[a] = (float)cheb_node(a);
-        cheb[kR + a] = (float)(((a & 1) ? -1.0 : 1.0) * std::sin((2 * a + 1) * M_PI / (2.0 * kR)));
-    }
-    // transfer: parent basis at child nodes, child at (t - 1)/2 (left) or (t + 1)/2 (right)
-    std::vector<float> tlr(2 * kR * kR);
-    for (int side = 0; side < 2; ++side)
-        for (int a = 0; a < kR; ++a)
-            for (int a2 = 0; a2 < kR; ++a2)
-                tlr[(side * kR + a) * kR + a2] =
-                    (float)cheb_lagrange(a, 0.5 * (cheb_node(a2) + (side ? 1.0 : -1.0)));
-    // interaction lists and M2L kernels 1 / (2 cos th - 2 cos ph) at the box nodes
-    const int nbox = (1 << (L + 1)) - 1;
-    std::vector<int> il((size_t)nbox * 3, -1);
-    std::vector<float> m2l((size_t)nbox * 3 * kR * kR, 0.0f);
-    for (int l = 2; l <= L; ++l) {
-        const int nb = 1 << l;
-        const double hw = 0.5 * M_PI / nb;
-        for (int I = 0; I < nb; ++I) {
-            int q = 0;
-            int pI = I >> 1;
-            for (int pj = pI - 1; pj <= pI + 1; ++pj) {
-                if (pj < 0 || pj >= (nb >> 1)) continue;
-                for (int J = 2 * pj; J <= 2 * pj + 1; ++J) {
-                    if (std::abs(J - I) <= 1) continue;
-                    size_t slot = (size_t)((1 << l) - 1 + I) * 3 + q;
-                    il[slot] = J;
-                    double cI = (I + 0.5) * 2 * hw, cJ = (J + 0.5) * 2 * hw;
-                    for (int a = 0; a < kR; ++a)
-                        for (int b = 0; b < kR; ++b) {
-                            double phi = cI + hw * cheb_node(a), th = cJ + hw * cheb_node(b);
-                            double den = 4.0 * std::sin(0.5 * (phi + th)) * std::sin(0.5 * (phi - th));
-                            m2l[(slot * kR + a) * kR + b] = (float)(1.0 / den);
-                        }
-                    ++q;
-                }
+    // leaf-to-leaf kernel 1 / (mu - lambda) = 1 / (2 cos th - 2 cos ph) at the
+    // Chebyshev nodes of target leaf I (ph) and source leaf J (th), |I - J| >= 2;
+    // rows (I, a), columns (J, b), zero-padded to ncp x ncp
+    h->nc = nleaf * kR;
+    h->ncp = (h->nc + 127) / 128 * 128;
+    const int nc = h->nc, ncp = h->ncp;
+    std::vector<float> kf_hi((size_t)ncp * ncp, 0.0f), kf_lo((size_t)ncp * ncp, 0.0f);
+    {
+        const double hw = 0.5 * hleaf;
+        std::vector<double> node(nc);
+        for (int I = 0; I < nleaf; ++I)
+            for (int a = 0; a < kR; ++a) node[I * kR + a] = (I + 0.5) * hleaf + hw * cheb_node(a);
+        for (int ia = 0; ia < nc; ++ia) {
+            const int I = ia / kR;
+            const double phi = node[ia];
+            for (int jb = 0; jb < nc; ++jb) {
+                const int J = jb / kR;
+                if (std::abs(I - J) <= 1) continue;
+                const double th = node[jb];
+                const double v = 1.0 / (4.0 * std::sin(0.5 * (phi + th)) * std::sin(0.5 * (phi - th)));
+                const float hi = tf32_host((float)v);
+                kf_hi[(size_t)ia * ncp + jb] = hi;
+                kf_lo[(size_t)ia * ncp + jb] = tf32_host((float)(v - (double)hi));
             }
         }
     }
@@ -252,14 +249,11 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     };
     DCTPLUS_CUDA_TRY(up(&h->zf, zf));
     DCTPLUS_CUDA_TRY(up(&h->tq, tq));
-    DCTPLUS_CUDA_TRY(up(&h->pu, pu));
     DCTPLUS_CUDA_TRY(up(&h->pna, pna));
     DCTPLUS_CUDA_TRY(up(&h->wl, wl));
-    DCTPLUS_CUDA_TRY(up(&h->cheb, cheb));
     DCTPLUS_CUDA_TRY(up(&h->row_leaf, row_leaf));
-    DCTPLUS_CUDA_TRY(up(&h->tlr, tlr));
-    DCTPLUS_CUDA_TRY(up(&h->m2l, m2l));
-    DCTPLUS_CUDA_TRY(up(&h->il, il));
+    DCTPLUS_CUDA_TRY(up(&h->kf_hi, kf_hi));
+    DCTPLUS_CUDA_TRY(up(&h->kf_lo, kf_lo));
     DCTPLUS_CUDA_TRY(up(&h->out_w, outw));
 
     int* d_kbeg = nullptr;
@@ -280,220 +274,134 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
 
 // ------------------------------------------------------------- far field
 
-struct FarArgs {
-    int n, nleaf, L, nout;
-    const float* zf;
-    const float* tq;
-    const float* pna;
-    const float* wl;
-    const int* row_leaf;
-    const float* tlr;
-    const float* m2l;
-    const int* il;
-    const float* out_w;
-    int out_row0, out_row1;
-};
-
-constexpr int kFarThreads = 512;
-
-// QS consecutive signals (a quad when NS >= 4) of the NS held in shared memory
-template <int QS>
-struct Vq {
-    float v[QS];
-};
-template <int QS>
-__device__ __forceinline__ Vq<QS> ldq(const float* p) {
-    Vq<QS> r;
-    if constexpr (QS == 4) {
-        const float4 t = *reinterpret_cast<const float4*>(p);
-        r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-    } else {
-#pragma unroll
-        for (int g = 0; g < QS; ++g) r.v[g] = p[g];
-    }
-    return r;
+// the TF32 remainder of v for an operand whose hi part is v itself (the MMA
+// reads v truncated to TF32)
+__device__ __forceinline__ float lo_of(float v) {
+    return __uint_as_float(ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu)));
 }
 
-// One CTA per group of NS signals: y[b] += far-field part of W s_b (and the
-// dense rows). Every phase splits its work into items of QS signals so that
-// all threads stay busy; coefficient arrays are [node][a][signal] so an item
-// reads its QS values with one vector load.
-template <int NS>
-__global__ void __launch_bounds__(kFarThreads) k_far(FarArgs A, const float* __restrict__ s, int64_t lds,
-                                                     float* __restrict__ y, int64_t ldy, int64_t batch) {
-    constexpr int QS = NS < 4 ? NS : 4;
-    constexpr int NQ = NS / QS;
-    extern __shared__ __align__(16) float fsm[];
-    const int n = A.n, nleaf = A.nleaf, L = A.L;
-    const int nbox = (1 << (L + 1)) - 1;
-    float* sv = fsm;                      // NS x n
-    float* zf = sv + NS * n;              // n
-    float* M = zf + n;                    // nbox x R x NS multipole coefficients
-    float* Lc = M + nbox * kR * NS;       // nbox x R x NS local coefficients
-    float* tq = Lc + nbox * kR * NS;      // 64 x R
-    float* tlr = tq + kLeaf * kR;         // 2 x R x R
-    float* red = tlr + 2 * kR * kR;       // (threads / 32) x NS
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < kLeaf * kR; e += nt) tq[e] = A.tq[e];
-    for (int e = tid; e < 2 * kR * kR; e += nt) tlr[e] = A.tlr[e];
-    for (int e = tid; e < n; e += nt) zf[e] = A.zf[e];
-    const int n4 = n / 4;  // n is a power of two >= 256 and lds % 4 == 0 (checked by the launcher)
-    for (int64_t b0 = (int64_t)blockIdx.x * NS; b0 < batch; b0 += (int64_t)gridDim.x * NS) {
-        const int ns = (int)min((int64_t)NS, batch - b0);
-        __syncthreads();
-        {
-            float4* sv4 = reinterpret_cast<float4*>(sv);
+// P2M: mc[b][lf R + a] = sum over the 64 sources j of leaf lf of z_j S_a(u_j) s_bj
+// (and its TF32 remainder), and for each dense row o the partial dot product
+// po[b][2 lf + o] = sum over the same sources of out_w[o][j] s_bj. A warp takes
+// one leaf of 32 signals: it copies the 32 x 64 source block into shared
+// memory with coalesced loads (rows padded to 68 floats, so the per-signal
+// reads below are conflict-free), then each lane forms the values of its
+// signal; z, the S_a table and the dense rows are broadcast.
+constexpr int kP2mPitch = kLeaf + 4;
+__global__ void __launch_bounds__(256) k_p2m(int nleaf, const float* __restrict__ zf,
+                                             const float* __restrict__ tq, const float* __restrict__ s,
+                                             int64_t lds, int64_t batch, float* __restrict__ mc,
+                                             float* __restrict__ mc_lo, int ldm, int n, int nout,
+                                             const float* __restrict__ out_w, float* __restrict__ po) {
+    __shared__ __align__(16) float tqs[kLeaf * kR];
+    extern __shared__ __align__(16) float p2m_tile[];  // 8 warps x 32 x kP2mPitch
+    for (int e = threadIdx.x; e < kLeaf * kR; e += blockDim.x) tqs[e] = tq[e];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lf = blockIdx.y * 8 + warp;
+    if (lf >= nleaf) return;
+    const int64_t b0 = (int64_t)blockIdx.x * 32;
+    float* tile = p2m_tile + warp * 32 * kP2mPitch;
 #pragma unroll 4
-            for (int e = tid; e < NS * n4; e += nt) {
-                const int g = e / n4, j4 = e - g * n4;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (g < ns) v = __ldg(reinterpret_cast<const float4*>(s + (b0 + g) * lds) + j4);
-                sv4[e] = v;
+    for (int k = 0; k < 16; ++k) {
+        const int row = 2 * k + (lane >> 4), c4 = lane & 15;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (b0 + row < batch)
+            v = *reinterpret_cast<const float4*>(s + (b0 + row) * lds + (int64_t)lf * kLeaf + 4 * c4);
+        *reinterpret_cast<float4*>(tile + row * kP2mPitch + 4 * c4) = v;
+    }
+    __syncwarp();
+    const float4* zp = reinterpret_cast<const float4*>(zf + (int64_t)lf * kLeaf);
+    const float* mine = tile + lane * kP2mPitch;
+    float acc[kR];
+#pragma unroll
+    for (int a = 0; a < kR; ++a) acc[a] = 0.f;
+    float od[2] = {0.f, 0.f};
+#pragma unroll 4
+    for (int j4 = 0; j4 < kLeaf / 4; ++j4) {
+        const float4 zv = __ldg(zp + j4);
+        const float4 sv = *reinterpret_cast<const float4*>(mine + 4 * j4);
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            if (o < nout) {
+                const float4 wv = __ldg(reinterpret_cast<const float4*>(out_w + (int64_t)o * n + (int64_t)lf * kLeaf) + j4);
+                od[o] = fmaf(wv.x, sv.x, fmaf(wv.y, sv.y, fmaf(wv.z, sv.z, fmaf(wv.w, sv.w, od[o]))));
             }
         }
-        __syncthreads();
-        // P2M at the leaves: M[leaf][a] = sum_jj z_j S_a(u_jj) s_j
-        for (int e = tid; e < nleaf * kR * NQ; e += nt) {
-            const int q = e % NQ, la = e / NQ, lf = la / kR, a = la % kR;
-            float acc[QS];
+        const float w[4] = {sv.x * zv.x, sv.y * zv.y, sv.z * zv.z, sv.w * zv.w};
 #pragma unroll
-            for (int g = 0; g < QS; ++g) acc[g] = 0.f;
-            const float* sq = sv + (q * QS) * n + lf * kLeaf;
-            for (int jj = 0; jj < kLeaf; jj += 4) {
-                const int j = lf * kLeaf + jj;
-                const float w0 = zf[j] * tq[jj * kR + a], w1 = zf[j + 1] * tq[(jj + 1) * kR + a];
-                const float w2 = zf[j + 2] * tq[(jj + 2) * kR + a], w3 = zf[j + 3] * tq[(jj + 3) * kR + a];
+        for (int e = 0; e < 4; ++e) {
+            const float4* t = reinterpret_cast<const float4*>(tqs + (4 * j4 + e) * kR);
 #pragma unroll
-                for (int g = 0; g < QS; ++g) {
-                    const float4 v = *reinterpret_cast<const float4*>(sq + g * n + jj);
-                    acc[g] = fmaf(w0, v.x, fmaf(w1, v.y, fmaf(w2, v.z, fmaf(w3, v.w, acc[g]))));
-                }
+            for (int q = 0; q < kR / 4; ++q) {
+                const float4 tv = t[q];
+                acc[4 * q + 0] = fmaf(w[e], tv.x, acc[4 * q + 0]);
+                acc[4 * q + 1] = fmaf(w[e], tv.y, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(w[e], tv.z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(w[e], tv.w, acc[4 * q + 3]);
             }
-            float* out = M + ((nleaf - 1 + lf) * kR + a) * NS + q * QS;
-#pragma unroll
-            for (int g = 0; g < QS; ++g) out[g] = acc[g];
         }
-        __syncthreads();
-        // M2M up to level 2
-        for (int l = L - 1; l >= 2; --l) {
-            const int nb = 1 << l;
-            for (int e = tid; e < nb * kR * NQ; e += nt) {
-                const int q = e % NQ, ba = e / NQ, bx = ba / kR, a = ba % kR;
-                const float* ml = M + ((2 << l) - 1 + 2 * bx) * kR * NS + q * QS;
-                const float* mr = ml + kR * NS;
-                float acc[QS];
+    }
+    const int64_t b = b0 + lane;
+    if (b >= batch) return;
+    float4* out = reinterpret_cast<float4*>(mc + b * ldm + (int64_t)lf * kR);
+    float4* olo = reinterpret_cast<float4*>(mc_lo + b * ldm + (int64_t)lf * kR);
 #pragma unroll
-                for (int g = 0; g < QS; ++g) acc[g] = 0.f;
+    for (int q = 0; q < kR / 4; ++q) {
+        out[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        olo[q] = make_float4(lo_of(acc[4 * q]), lo_of(acc[4 * q + 1]), lo_of(acc[4 * q + 2]),
+                             lo_of(acc[4 * q + 3]));
+    }
 #pragma unroll
-                for (int a2 = 0; a2 < kR; ++a2) {
-                    const float tl = tlr[a * kR + a2], tr = tlr[(kR + a) * kR + a2];
-                    const Vq<QS> vl = ldq<QS>(ml + a2 * NS), vr = ldq<QS>(mr + a2 * NS);
-#pragma unroll
-                    for (int g = 0; g < QS; ++g) acc[g] = fmaf(tl, vl.v[g], fmaf(tr, vr.v[g], acc[g]));
-                }
-                float* out = M + ((nb - 1 + bx) * kR + a) * NS + q * QS;
-#pragma unroll
-                for (int g = 0; g < QS; ++g) out[g] = acc[g];
-            }
-            __syncthreads();
+    for (int o = 0; o < 2; ++o)
+        if (o < nout) po[b * 2 * nleaf + 2 * lf + o] = od[o];
+}
+
+// L2P: y[b][r] += sum_a wl[a][r] lc[b][leaf(r) R + a] for the far-field targets.
+// A thread keeps row r's weights in registers for 8 signals (block x: 8
+// signals, block y: 256 consecutive rows). The extra block row y = n / 256
+// writes the dense rows (eigenvalue outside [0, 4]): warp w sums, across its
+// lanes, the per-leaf partial dot products of signal 8 x + w.
+constexpr int kL2pSig = 8;
+__global__ void __launch_bounds__(256) k_l2p(int n, const float* __restrict__ wl,
+                                             const int* __restrict__ row_leaf,
+                                             const float* __restrict__ pna, const float* __restrict__ lc,
+                                             int ldm, float* __restrict__ y, int64_t ldy, int64_t batch,
+                                             int nleaf, int out_row0, int out_row1,
+                                             const float* __restrict__ po) {
+    const int64_t b0 = (int64_t)blockIdx.x * kL2pSig;
+    if ((int)blockIdx.y * 256 >= n) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int64_t b = b0 + w;
+        if (w >= kL2pSig || b >= batch) return;
+        for (int o = 0; o < 2; ++o) {
+            const int row = o == 0 ? out_row0 : out_row1;
+            if (row < 0) continue;
+            float t = 0.f;
+            for (int lf = lane; lf < nleaf; lf += 32) t += po[b * 2 * nleaf + 2 * lf + o];
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == 0) y[b * ldy + row] = t;
         }
-        // M2L at every level >= 2 (nodes of levels >= 2 start at index 3)
-        for (int e = tid; e < (nbox - 3) * kR * NQ; e += nt) {
-            const int q = e % NQ, na = e / NQ, node = 3 + na / kR, a = na % kR;
-            const int lvl = 31 - __clz(node + 1);
-            float acc[QS];
+        return;
+    }
+    const int r = blockIdx.y * 256 + threadIdx.x;
+    if (pna[r] == 0.f) return;
+    float w[kR];
 #pragma unroll
-            for (int g = 0; g < QS; ++g) acc[g] = 0.f;
-            for (int q3 = 0; q3 < 3; ++q3) {
-                const int J = A.il[node * 3 + q3];
-                if (J < 0) continue;
-                const float* mj = M + ((1 << lvl) - 1 + J) * kR * NS + q * QS;
-                const float* k = A.m2l + ((size_t)(node * 3 + q3) * kR + a) * kR;
-                float kv[kR];
+    for (int a = 0; a < kR; ++a) w[a] = __ldg(wl + (int64_t)a * n + r);
+    const int leaf = row_leaf[r];
+#pragma unroll 2
+    for (int g = 0; g < kL2pSig; ++g) {
+        const int64_t b = b0 + g;
+        if (b >= batch) break;
+        const float4* l4 = reinterpret_cast<const float4*>(lc + b * ldm + (int64_t)leaf * kR);
+        float acc = 0.f;
 #pragma unroll
-                for (int b2 = 0; b2 < kR; ++b2) kv[b2] = __ldg(k + b2);
-#pragma unroll
-                for (int b2 = 0; b2 < kR; ++b2) {
-                    const Vq<QS> v = ldq<QS>(mj + b2 * NS);
-#pragma unroll
-                    for (int g = 0; g < QS; ++g) acc[g] = fmaf(kv[b2], v.v[g], acc[g]);
-                }
-            }
-            float* out = Lc + (node * kR + a) * NS + q * QS;
-#pragma unroll
-            for (int g = 0; g < QS; ++g) out[g] = acc[g];
+        for (int q = 0; q < kR / 4; ++q) {
+            const float4 l = l4[q];
+            acc = fmaf(w[4 * q], l.x, fmaf(w[4 * q + 1], l.y, fmaf(w[4 * q + 2], l.z, fmaf(w[4 * q + 3], l.w, acc))));
         }
-        __syncthreads();
-        // L2L down to the leaves
-        for (int l = 2; l < L; ++l) {
-            const int nb = 1 << l;
-            for (int e = tid; e < 2 * nb * kR * NQ; e += nt) {
-                const int q = e % NQ, ca = e / NQ, c = ca / kR, a2 = ca % kR;  // child box at level l + 1
-                const int side = c & 1;
-                const float* lp = Lc + (nb - 1 + (c >> 1)) * kR * NS + q * QS;
-                float acc[QS];
-#pragma unroll
-                for (int g = 0; g < QS; ++g) acc[g] = 0.f;
-#pragma unroll
-                for (int a = 0; a < kR; ++a) {
-                    const float t = tlr[(side * kR + a) * kR + a2];
-                    const Vq<QS> v = ldq<QS>(lp + a * NS);
-#pragma unroll
-                    for (int g = 0; g < QS; ++g) acc[g] = fmaf(t, v.v[g], acc[g]);
-                }
-                float* out = Lc + ((2 * nb - 1 + c) * kR + a2) * NS + q * QS;
-#pragma unroll
-                for (int g = 0; g < QS; ++g) out[g] += acc[g];
-            }
-            __syncthreads();
-        }
-        // L2P: y_r += sum_a w[a][r] L[leaf(r)][a] with w = -a_r S_a(u_r) from the table
-        for (int e = tid; e < n * NQ; e += nt) {
-            const int q = e / n, r = e - q * n;
-            if (A.pna[r] == 0.f) continue;
-            const float* lc = Lc + (nleaf - 1 + A.row_leaf[r]) * kR * NS + q * QS;
-            float acc[QS];
-#pragma unroll
-            for (int g = 0; g < QS; ++g) acc[g] = 0.f;
-#pragma unroll
-            for (int a = 0; a < kR; ++a) {
-                const float w = __ldg(A.wl + (size_t)a * n + r);
-                const Vq<QS> v = ldq<QS>(lc + a * NS);
-#pragma unroll
-                for (int g = 0; g < QS; ++g) acc[g] = fmaf(w, v.v[g], acc[g]);
-            }
-            float yv[QS];
-#pragma unroll
-            for (int g = 0; g < QS; ++g) yv[g] = (q * QS + g < ns) ? y[(b0 + q * QS + g) * ldy + r] : 0.f;
-#pragma unroll
-            for (int g = 0; g < QS; ++g)
-                if (q * QS + g < ns) y[(b0 + q * QS + g) * ldy + r] = yv[g] + acc[g];
-        }
-        // dense rows
-        for (int o = 0; o < A.nout; ++o) {
-            const float* w = A.out_w + (size_t)o * n;
-            float acc[NS];
-#pragma unroll
-            for (int g = 0; g < NS; ++g) acc[g] = 0.f;
-            for (int j = tid; j < n; j += nt) {
-                const float wj = w[j];
-#pragma unroll
-                for (int g = 0; g < NS; ++g) acc[g] = fmaf(wj, sv[g * n + j], acc[g]);
-            }
-#pragma unroll
-            for (int g = 0; g < NS; ++g) {
-                float v = acc[g];
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if ((tid & 31) == 0) red[(tid >> 5) * NS + g] = v;
-            }
-            __syncthreads();
-            if (tid < ns) {
-                float t = 0.f;
-                for (int w2 = 0; w2 < nt / 32; ++w2) t += red[w2 * NS + tid];
-                y[(b0 + tid) * ldy + (o == 0 ? A.out_row0 : A.out_row1)] = t;
-            }
-            __syncthreads();
-        }
+        y[b * ldy + r] += acc;
     }
 }
 
@@ -509,58 +417,45 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     const int n = p->n;
     if (!h || batch > INT32_MAX || (reinterpret_cast<uintptr_t>(y) & 15) || (ldy & 3))
         return DCTPLUS_ERR_UNSUPPORTED;
-    const size_t plane = (size_t)batch * n;
-    float* ws = static_cast<float*>(plan_workspace(p, st, 2 * sizeof(float) * plane));
+    if (batch <= 0) return DCTPLUS_OK;
+    const size_t plane = (size_t)batch * n, cplane = (size_t)batch * h->ncp;
+    const size_t pplane = (size_t)batch * 2 * h->nleaf;
+    float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * (2 * plane + 3 * cplane + pplane)));
     if (!ws) return DCTPLUS_ERR_CUDA;
-    dctplus_status r = launch_dct_fft(p, x, ldx, ws, ws + plane, n, batch, st);
+    float* s_hi = ws;
+    float* s_lo = ws + plane;
+    float* mc = ws + 2 * plane;
+    float* mc_lo = mc + cplane;
+    float* lc = mc_lo + cplane;
+    float* po = lc + cplane;  // batch x 2 nleaf: the dense rows' per-leaf partial sums
+    dctplus_status r = launch_dct_fft(p, x, ldx, s_hi, s_lo, n, batch, st);
     if (r != DCTPLUS_OK) return r;
-    r = launch_gemm_tc_band(ws, ws + plane, n, n, h->slab_hi, h->slab_lo, h->Kw, y, ldy, (int)batch,
-                            n, h->Kw, h->kbeg.data(), st, p->device);
-    if (r != DCTPLUS_OK) return r;
-    FarArgs A;
-    A.n = n;
-    A.nleaf = h->nleaf;
-    A.L = h->L;
-    A.nout = h->nout;
-    A.zf = h->zf;
-    A.tq = h->tq;
-    A.pna = h->pna;
-    A.wl = h->wl;
-    A.row_leaf = h->row_leaf;
-    A.tlr = h->tlr;
-    A.m2l = h->m2l;
-    A.il = h->il;
-    A.out_w = h->out_w;
-    A.out_row0 = h->out_row[0];
-    A.out_row1 = h->out_row[1];
-    const int nbox = (1 << (h->L + 1)) - 1;
-    auto smem_for = [&](int ns) {
-        return sizeof(float) * ((size_t)ns * n + n + 2 * (size_t)nbox * kR * ns + kLeaf * kR +
-                                2 * kR * kR + (kFarThreads / 32) * ns);
-    };
-    const size_t cap = 100 * 1024;  // several CTAs per SM
-    int ns = 16;
-    while (ns > 1 && smem_for(ns) > cap) ns >>= 1;
-    const size_t smem = smem_for(ns);
-    int64_t groups = (batch + ns - 1) / ns;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    const int per_sm = std::max(1, std::min((int)(220 * 1024 / smem), 2048 / kFarThreads));
-    int64_t grid = std::min<int64_t>(groups, (int64_t)std::max(sms, 1) * per_sm);
-    auto launch = [&](auto kern) -> dctplus_status {
-        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)grid, kFarThreads, smem, st>>>(A, ws, n, y, ldy, batch);
-        count_launch();
-        DCTPLUS_CUDA_TRY(cudaGetLastError());
-        return DCTPLUS_OK;
-    };
-    switch (ns) {
-        case 16: return launch(k_far<16>);
-        case 8: return launch(k_far<8>);
-        case 4: return launch(k_far<4>);
-        case 2: return launch(k_far<2>);
-        default: return launch(k_far<1>);
+    // far field first, while s is still in L2: leaf coefficients (and the dense
+    // rows' per-leaf partial sums), then the leaf-to-leaf product
+    const size_t p2m_smem = sizeof(float) * 8 * 32 * kP2mPitch;  // 69.6 KB
+    static bool p2m_attr[64] = {};
+    if (!p2m_attr[p->device & 63]) {
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem));
+        p2m_attr[p->device & 63] = true;
     }
+    k_p2m<<<dim3((unsigned)((batch + 31) / 32), (unsigned)((h->nleaf + 7) / 8)), 256, p2m_smem, st>>>(
+        h->nleaf, h->zf, h->tq, s_hi, n, batch, mc, mc_lo, h->ncp, n, h->nout, h->out_w, po);
+    count_launch();
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    r = launch_gemm_tc_band(mc, mc_lo, h->ncp, h->nc, h->kf_hi, h->kf_lo, h->ncp, lc, h->ncp,
+                            (int)batch, h->ncp, h->ncp, nullptr, st, p->device);
+    if (r != DCTPLUS_OK) return r;
+    // near field: y = band of W applied to s (dense rows get 0 here)
+    r = launch_gemm_tc_band(s_hi, s_lo, n, n, h->slab_hi, h->slab_lo, h->Kw, y, ldy, (int)batch, n,
+                            h->Kw, h->kbeg.data(), st, p->device);
+    if (r != DCTPLUS_OK) return r;
+    // far field added into y; the dense rows from their partial sums
+    k_l2p<<<dim3((unsigned)((batch + kL2pSig - 1) / kL2pSig), (unsigned)(n / 256 + (h->nout > 0))), 256, 0, st>>>(
+        n, h->wl, h->row_leaf, h->pna, lc, h->ncp, y, ldy, batch, h->nleaf,
+        h->nout > 0 ? h->out_row[0] : -1, h->nout > 1 ? h->out_row[1] : -1, po);
+    count_launch();
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
 }
 
 }  // namespace dctplus
