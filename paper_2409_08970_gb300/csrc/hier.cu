@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(256) k_p2m(int nleaf, const float* __restrict_
     if (lf >= nleaf) return;
     const int64_t b0 = (int64_t)blockIdx.x * 32;
     float* tile = p2m_tile + warp * 32 * kP2mPitch;
-#pragma unroll 4
-    for (int k = 0; k < 16; ++k) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {  // all 16 loads in flight
         const int row = 2 * k + (lane >> 4), c4 = lane & 15;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (b0 + row < batch)
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(256) k_l2p(int n, const float* __restrict__ wl
 #pragma unroll
     for (int a = 0; a < kR; ++a) w[a] = __ldg(wl + (int64_t)a * n + r);
     const int leaf = row_leaf[r];
-#pragma unroll 2
+#pragma unroll 4
     for (int g = 0; g < kL2pSig; ++g) {
         const int64_t b = b0 + g;
         if (b >= batch) break;
