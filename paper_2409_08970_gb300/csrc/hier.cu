@@ -1,5 +1,5 @@
-// Hierarchical O(n log n) evaluation of the Cauchy product of Theorem 3.1
-// (the fast matrix-vector product Theorem 3.2 relies on, in the Gerasoulis /
+// Hierarchical evaluation of the Cauchy product of Theorem 3.1 (the fast
+// matrix-vector product Theorem 3.2 relies on, in the Gerasoulis /
 // fast-multipole family), for a batch of signals.
 //
 // The product is y_r = sum_j W_rj s_j with W_rj = -a_r z_j / (mu_r - lambda_j)
@@ -9,8 +9,8 @@
 // a kernel of (ph, th) that is analytic away from th = +-ph, so Chebyshev
 // interpolation in th over a box of width h is accurate for targets at least
 // one box away (convergence factor 3 + sqrt(8) per degree). Sources are
-// uniform in th, so a binary tree of equal th-boxes with 64 sources per leaf
-// is balanced; targets interlace the sources (Lemma 4.1), about 64 per leaf.
+// uniform in th, so equal th-boxes ("leaves") of 64 sources each are
+// balanced; targets interlace the sources (Lemma 4.1), about 64 per leaf.
 //
 //   near field  targets of leaf I against sources of leaves I-1, I, I+1: exact
 //               entries of W, a band matrix applied on the tensor cores with
@@ -24,12 +24,14 @@
 //               source leaf J, |I - J| >= 2), a [nleaf R x nleaf R] matrix on
 //               the tensor cores (split-TF32 GEMM), then L2P (-a folded into
 //               the weights, CUDA cores) added into y. A single level with a
-//               dense leaf-to-leaf operator trades the tree's O(n) M2L work for
-//               (12 n / 64)^2 tensor-core multiply-adds per signal, fewer than
-//               the dense product's n^2 by (64 / 12)^2.
+//               dense leaf-to-leaf operator trades a multilevel tree's O(n)
+//               translation work for (12 n / 64)^2 tensor-core multiply-adds
+//               per signal, fewer than the dense product's n^2 by (64 / 12)^2,
+//               and needs no barriers between tree levels.
 // Roots outside [0, 4] (at most the largest for rho > 0 or the smallest for
 // rho < 0; the paper's pre-processing isolates the same root) have no real
-// angle; their rows are dense dot products.
+// angle; their rows are dense dot products, formed as per-leaf partial sums
+// by P2M and summed by L2P.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
