@@ -18,7 +18,11 @@
 //   warp 0      TMA producer: A_hi, A_lo, B_hi, B_lo K-slices of 32 (3 stages)
 //   warp 1      TMEM owner (256 columns: two 128-column chunk buffers), MMA issuer
 //   warps 2..9  chunk promotion into registers, final store; two warps per
-//               TMEM lane quarter, 64 columns each
+//               TMEM lane quarter, 64 columns each. A warp writes its 32 x 64
+//               block as two 32 x 32 boxes staged in its own 4 KB of shared
+//               memory and stored by TMA (rows past M are clipped): stores of
+//               rows straight from registers would put 32 partial-sector L2
+//               writes per instruction into the load/store unit.
 // Bounded waits as in the small-n kernel.
 #include <cudaTypedefs.h>
 
@@ -39,7 +43,8 @@ constexpr int kThreads = 320;
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr uint32_t kSlice = kBM * kBK * 4;           // 16 KB: one 128 x 32 FP32 slice
 constexpr uint32_t kStageBytes = 4 * kSlice;          // A_hi, A_lo, B_hi, B_lo
-constexpr uint32_t kOffBar = kStages * kStageBytes;
+constexpr uint32_t kOffY = kStages * kStageBytes;     // 8 warps x 4 KB output staging
+constexpr uint32_t kOffBar = kOffY + 8 * 4096;
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;
 
 constexpr int kMaxTilesN = 128;
@@ -49,6 +54,7 @@ constexpr int kMaxTilesN = 128;
 // (a band; A columns outside [0, Ka) read as zeros).
 struct Params {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
+    CUtensorMap y_map;  // y [M x N], box 32 x 32, 128-byte swizzle
     float* y;
     int64_t ldy;
     int M, N, K;
@@ -175,15 +181,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 if (lane == 0) ptx::mbar_arrive(&acc_empty[b]);
             }
             if (!ok) break;
-            const int row = m0 + r;
-            if (row < P.M) {
-                float* yr = P.y + (int64_t)row * P.ldy + n0 + 64 * h;
+            unsigned char* ys = sm + kOffY + (warp - 2) * 4096;
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    reinterpret_cast<float4*>(yr)[j] =
-                        make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+            for (int c = 0; c < 2; ++c) {
+                // the previous box from this buffer has been read by its store
+                if (lane == 0) ptx::bulk_wait_group_read0();
+                __syncwarp();
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc)
+                    *reinterpret_cast<float4*>(ys + lane * 128 + ((cc ^ (lane & 7)) << 4)) =
+                        make_float4(acc[32 * c + 4 * cc], acc[32 * c + 4 * cc + 1], acc[32 * c + 4 * cc + 2],
+                                    acc[32 * c + 4 * cc + 3]);
+                ptx::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    ptx::tma_store_2d(&P.y_map, n0 + 64 * h + 32 * c, m0 + 32 * q, ys);
+                    ptx::bulk_commit_group();
+                }
             }
         }
+        if (lane == 0) ptx::bulk_wait_group0();
         if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
     }
 
@@ -211,13 +228,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn_g() {
     return fn;
 }
 
-// rows x cols FP32 row-major (leading dimension ld floats), box 32 x 128, 128-byte swizzle
-static bool encode_rows(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld) {
+// rows x cols FP32 row-major (leading dimension ld floats), box 32 x box_rows, 128-byte swizzle
+static bool encode_rows(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld,
+                        int box_rows = 128) {
     auto fn = encode_fn_g();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
-    cuuint32_t box[2] = {32, 128};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -235,7 +253,7 @@ dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t
                                    cudaStream_t s, int dev) {
     if (M <= 0) return DCTPLUS_OK;
     if (K % gemm::kBK || N % gemm::kBN || (lda & 3) || (ldb & 3) || (ldy & 3) ||
-        N / gemm::kBN > gemm::kMaxTilesN)
+        N / gemm::kBN > gemm::kMaxTilesN || (reinterpret_cast<uintptr_t>(y) & 15))
         return DCTPLUS_ERR_UNSUPPORTED;
     static bool attr[64] = {};
     if (!attr[dev & 63]) {
@@ -246,7 +264,8 @@ dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t
     gemm::Params P;
     memset(&P, 0, sizeof(P));
     if (!encode_rows(&P.a_hi, a_hi, M, Ka, lda) || !encode_rows(&P.a_lo, a_lo, M, Ka, lda) ||
-        !encode_rows(&P.b_hi, b_hi, N, K, ldb) || !encode_rows(&P.b_lo, b_lo, N, K, ldb))
+        !encode_rows(&P.b_hi, b_hi, N, K, ldb) || !encode_rows(&P.b_lo, b_lo, N, K, ldb) ||
+        !encode_rows(&P.y_map, y, M, N, ldy, 32))
         return DCTPLUS_ERR_CUDA;
     P.y = y;
     P.ldy = ldy;
