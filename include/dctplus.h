@@ -144,6 +144,12 @@ int dctplus_plan_cauchy_mode(dctplus_plan_t plan);
  *           multiples of 4; other layouts take the CUDA-core kernels.
  *           x and y must not overlap.
  *   batch : number of signals, >= 0 (0 is a no-op).
+ * Scratch: for n >= 128 the plan keeps a device workspace per stream, grown
+ * on the first call that needs more: 2 batch n floats (the DCT coefficients
+ * and their TF32 remainder); the hierarchical mode adds 3 batch c floats
+ * (c = 12 n / 64 rounded up to 128) and batch n / 32 floats. A call that grows
+ * it allocates, so make the first call at the largest batch before capturing
+ * the stream into a CUDA graph.
  * Asynchronous on `stream`. Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const void* x_dev,
                                int64_t ldx, void* y_dev, int64_t ldy, int64_t batch,
