@@ -507,7 +507,8 @@ def run_reference(args):
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rows": int(wl.total_rows), "samples": int(wl.total_samples)},
+            "config": {"workload": WORKLOAD, "rows": int(wl.total_rows), "samples": int(wl.total_samples),
+                       "segments": len(wl.segments), "parallelism": "host cores (FP64 oracle)"},
             "cpu_baseline": {"value": value, "unit": "GSamples/s", "cores": cores, "kind": "oracle",
                              "sample": "the whole workload per step (FP64 Cauchy-formula oracle, "
                                        "numpy/BLAS on the host cores, plans excluded)"},
