@@ -44,6 +44,96 @@ def load_peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+# TF32 dense tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s per GPU): the peak of
+# the split-TF32 contractions is the measured BF16 cuBLAS figure times this ratio.
+TF32_PER_BF16 = 1.1 / 2.25
+# FP64 on the CUDA cores (nominal, no measured figure): 1.25 TFLOP/s
+FP64_NOMINAL_TFLOPS = 1.25
+TENSOR_KERNELS = ("k_gemm_tc", "k_small_tc")
+
+
+def trace_kernels(pkg, torch, stream, step, flush, reps=3):
+    """Per-launch device time of one step, from the library's kernel trace (CUDA events after
+    every launch on the step's stream, outside graph capture, L2 flushed before each step).
+    Returns one record per launch position: name, median ms over reps, bytes, flops."""
+    sh = stream.cuda_stream
+    runs = []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush()
+        pkg.dctplus_trace_begin(sh)
+        step()
+        runs.append(pkg.dctplus_trace_end(sh))
+    out = []
+    for i, rec in enumerate(runs[0]):
+        ms = float(np.median([r[i][1] for r in runs if len(r) > i]))
+        out.append({"kernel": rec[0], "ms": ms, "bytes": rec[2], "flops": rec[3]})
+    return out
+
+
+def roofline_of(recs, hbm_peak, bf16_peak, peak_src):
+    """Roofline object of the dominant kernel (largest summed time over the step's launches of
+    that kernel): tensor-bound for the tensor-core GEMMs (split-TF32 peak), HBM otherwise."""
+    by = {}
+    for r in recs:
+        e = by.setdefault(r["kernel"], {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "launches": 0})
+        e["ms"] += r["ms"]
+        e["bytes"] += r["bytes"]
+        e["flops"] += r["flops"]
+        e["launches"] += 1
+    total = sum(e["ms"] for e in by.values())
+    name, e = max(by.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = e["ms"] / e["launches"]
+    if name in TENSOR_KERNELS and name != "k_small_tc":
+        peak = bf16_peak * TF32_PER_BF16
+        achieved = e["flops"] / e["launches"] / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": f"{peak_src} bf16_tflops x {TF32_PER_BF16:.4f} (TF32/BF16 nominal "
+                               "1.1/2.25 PFLOP/s): split-TF32 products counted as executed",
+                "algorithmic_flops_per_launch": e["flops"] / e["launches"]}
+    else:
+        achieved = e["bytes"] / e["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+                "algorithmic_bytes_per_launch": e["bytes"] / e["launches"]}
+    roof.update({"kernel": name, "kernel_ms": per_launch_ms, "launches_of_kernel": e["launches"],
+                 "share_of_step": e["ms"] / total if total > 0 else None, "traffic": None,
+                 "stages": [{"kernel": r["kernel"], "ms": round(r["ms"], 5)} for r in recs]})
+    return roof
+
+
+def oracle_error(n, v, rho, x, y, sig_rows=8, root_sample=None, seed=7):
+    """FP32 output against the FP64 oracle (Cauchy formula) on a sampled subset of signals: all
+    rows up to n = 4096, else about 40 sampled secular-root rows. Errors relative to the
+    signal's norm (max) and normwise over the compared rows."""
+    from oracle import cauchy
+    rng = np.random.default_rng(seed)
+    sig = np.sort(rng.choice(x.shape[0], min(sig_rows, x.shape[0]), replace=False))
+    xs = x[sig].astype(np.float64)
+    if n <= 4096 and root_sample is None:
+        op = cauchy.make_plan(n, v, rho)
+        cols = np.arange(n)
+    else:
+        probe = cauchy.make_plan(n, v, rho, roots=[])
+        K = int(probe.row_kind.sum())
+        roots = np.unique(np.concatenate([rng.choice(K, min(K, root_sample or 36), replace=False),
+                                          [0, K - 1]]))
+        op = cauchy.make_plan(n, v, rho, roots=roots)
+        cols = np.nonzero((op.row_kind == 1) & np.isin(op.row_index, roots))[0]
+    ref = cauchy.transform(op, xs, rows=cols)
+    got = y[sig][:, cols].astype(np.float64)
+    diff = got - ref
+    nrm = np.linalg.norm(xs, axis=1)
+    rel = np.linalg.norm(diff, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+    return {"max_abs": float(np.abs(diff).max()),
+            "max_abs_rel_to_signal_norm": float((np.abs(diff).max(axis=1) / nrm).max()),
+            "normwise_rel_max": float(rel.max()),
+            "snr_db_mean": float(np.mean(-20 * np.log10(np.maximum(rel, 1e-300)))),
+            "sample": f"{len(sig)} signals x {len(cols)} coefficients"
+                      + ("" if len(cols) == n else " (sampled secular-root rows)")}
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -264,13 +354,16 @@ def run_ours(args):
     extra = {}
     if not args.no_extra and rank == 0:
         D, H, G = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT
-        extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 1024, 4096, [H, D, G])
+        peaks = (hbm_peak, bf16_peak, peak_src)
+        errs = not args.no_cpu
+        extra["fp64_n64"] = bench_fp64_n64(pkg, torch, dev, stream, args, flush, peaks)
+        extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 1024, 4096, [H, D, G], errs)
         if not args.quick:
-            extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 256, 4096, [H, D, G])
-            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 4096, 4096, [H, D, G])
-            extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, 16384, 512, [H])
-        extra["pruned_n512"] = bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak)
-        extra["backward_n1024"] = bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak)
+            extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 256, 4096, [H, D, G], errs)
+            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 4096, 4096, [H, D, G], errs)
+            extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 16384, 512, [H], errs)
+        extra["pruned_n512"] = bench_pruned(pkg, torch, dev, stream, args, flush, peaks)
+        extra["backward_n1024"] = bench_backward(pkg, torch, dev, stream, args, flush, peaks)
         extra["dense_gft_cublas_fp32"] = bench_dense_gft(pkg, torch, dev, stream, args, flush, wl,
                                                          plans, seg)
     cpu = None
@@ -310,19 +403,27 @@ def run_ours(args):
 MODE_NAMES = {1: "dense", 2: "hierarchical", 3: "cuda_core", 4: "dense_gft_baseline"}
 
 
-def bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, n, batch, modes):
+def bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, errors=True):
     """Large-n forward: batch N(0,1) signals, dense unit v (seed 1), rho in {-0.3, 2.0};
-    one step = both plans over the batch. Modes are timed one after another."""
+    one step = both plans over the batch. Modes are timed one after another. Per mode: the
+    step rate, the dominant kernel's roofline (kernel trace), the plan time and the FP32 error
+    against the FP64 oracle on sampled signals."""
     from synthetic import normal_signals, random_unit_v
+    hbm_peak, bf16_peak, peak_src = peaks
     v = random_unit_v(n)
-    x = torch.tensor(normal_signals(batch, n, seed=0), dtype=torch.float32, device=dev)
+    xh = normal_signals(batch, n, seed=0)
+    x = torch.tensor(xh, dtype=torch.float32, device=dev)
     ys = [torch.empty_like(x) for _ in range(2)]
     sh = stream.cuda_stream
     samples = 2 * batch * n
-    out = {"workload": f"n={n}, batch {batch}, x~N(0,1), dense unit v (seed 1), rho in {{-0.3, 2.0}}"}
+    rhos = (-0.3, 2.0)
+    out = {"workload": f"n={n}, batch {batch}, x~N(0,1), dense unit v (seed 1), rho in {{-0.3, 2.0}}; "
+                       "one step = both plans over the batch"}
     for mode in modes:
         try:
-            plans = [pkg.Plan(n, v, rho, cauchy_mode=mode) for rho in (-0.3, 2.0)]
+            t0 = time.perf_counter()
+            plans = [pkg.Plan(n, v, rho, cauchy_mode=mode) for rho in rhos]
+            plan_ms = (time.perf_counter() - t0) * 1e3 / len(rhos)
         except pkg.DctPlusError:
             continue
 
@@ -336,30 +437,96 @@ def bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, n, batch, modes)
         launches = pkg.dctplus_launch_count() - lc
         times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
         t_ms = float(np.mean(times))
-        out[MODE_NAMES.get(plans[0].cauchy_mode, str(mode))] = {
-            "value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t_ms,
-            "launches_per_step": launches,
-            "hbm_frac_of_measured": 8.0 * samples / (t_ms * 1e-3) / 1e9 / hbm_peak}
+        recs = trace_kernels(pkg, torch, stream, step, flush)
+        entry = {"value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t_ms,
+                 "launches_per_step": launches,
+                 "hbm_frac_of_measured": 8.0 * samples / (t_ms * 1e-3) / 1e9 / hbm_peak,
+                 "plan_ms": plan_ms,
+                 "roofline": roofline_of(recs, hbm_peak, bf16_peak, peak_src)}
+        if errors:
+            step()
+            torch.cuda.synchronize()
+            errs = [oracle_error(n, v, rho, xh, y.cpu().numpy(),
+                                 root_sample=36 if n > 4096 else None) for rho, y in zip(rhos, ys)]
+            entry["fp32_err_vs_fp64_oracle"] = {
+                k: max(e[k] for e in errs) for k in ("max_abs", "max_abs_rel_to_signal_norm",
+                                                    "normwise_rel_max")}
+            entry["fp32_err_vs_fp64_oracle"]["snr_db_mean"] = float(np.mean([e["snr_db_mean"] for e in errs]))
+            entry["fp32_err_vs_fp64_oracle"]["sample"] = errs[0]["sample"] + " per plan"
+        out[MODE_NAMES.get(plans[0].cauchy_mode, str(mode))] = entry
         for p in plans:
             p.close()
     return out
 
 
-def bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak, n=512, batch=16384, m_out=128):
+def bench_fp64_n64(pkg, torch, dev, stream, args, flush, peaks):
+    """FP64 forward, n = 64, unit self-loop at vertex 0 (v = e_0, rho = 1), 1024 N(0,1)
+    signals (seed 0): the FP64 configuration, with its error against the FP64 oracle."""
+    from oracle import cauchy
+    from synthetic import normal_signals, self_loop_v
+    hbm_peak, bf16_peak, peak_src = peaks
+    n, batch = 64, 1024
+    v = self_loop_v(n, 0)
+    xh = normal_signals(batch, n, seed=0)
+    x = torch.tensor(xh, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    sh = stream.cuda_stream
+    t0 = time.perf_counter()
+    plan = pkg.Plan(n, v, 1.0)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+
+    def step():
+        pkg.dctplus_execute(plan.handle, pkg.F64, x.data_ptr(), n, y.data_ptr(), n, batch, sh)
+
+    times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
+    t_ms = float(np.mean(times))
+    recs = trace_kernels(pkg, torch, stream, step, flush)
+    step()
+    torch.cuda.synchronize()
+    ref = cauchy.transform(cauchy.make_plan(n, v, 1.0), xh)
+    got = y.cpu().numpy()
+    rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    k = recs[0]
+    achieved = k["flops"] / (k["ms"] * 1e-3) / 1e12
+    plan.close()
+    return {"workload": "FP64, n=64, self-loop weight 1 at vertex 0 (v=e_0), 1024 signals x~N(0,1) "
+                        "(seed 0)",
+            "value": batch * n / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t_ms,
+            "dtype": "f64", "plan_ms": plan_ms,
+            "err_vs_fp64_oracle": {"max_abs": float(np.abs(got - ref).max()),
+                                   "normwise_rel_max": float(rel.max())},
+            "roofline": {"bound": "alu", "kernel": k["kernel"], "kernel_ms": k["ms"],
+                         "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_NOMINAL_TFLOPS,
+                         "peak_source": "nominal FP64 CUDA-core rate (no measured FP64 figure)",
+                         "algorithmic_flops_per_launch": k["flops"],
+                         "note": "1024 signals: a few microseconds of work, launch-latency bound"}}
+
+
+def bench_pruned(pkg, torch, dev, stream, args, flush, peaks, n=512, batch=16384, m_out=128):
     """Progressive multi-transform with pruning (Theorem 3.4): one DCT-II per signal shared by
     K = 8 self-loop updates at vertex 0 (rho = 0.25 .. 2.0), the first m_out coefficients of
     each; exact (c_p = n) and truncated (c_p = m_out), against 8 independent full transforms."""
+    from oracle import cauchy
     from synthetic import normal_signals, self_loop_v
+    hbm_peak, bf16_peak, peak_src = peaks
     rhos = [0.25 * (k + 1) for k in range(8)]
+    t0 = time.perf_counter()
     plans = [pkg.Plan(n, self_loop_v(n, 0), r) for r in rhos]
-    x = torch.tensor(normal_signals(batch, n, seed=0), dtype=torch.float32, device=dev)
+    plan_ms = (time.perf_counter() - t0) * 1e3 / len(rhos)
+    xh = normal_signals(batch, n, seed=0)
+    x = torch.tensor(xh, dtype=torch.float32, device=dev)
     sh = stream.cuda_stream
     samples = batch * n
     width = len(plans) * m_out
     y = torch.empty(batch, width, dtype=torch.float32, device=dev)
     ys = [torch.empty_like(x) for _ in plans]
     out = {"workload": f"n={n}, batch {batch}, K=8 self-loop updates at vertex 0 (rho 0.25..2.0), "
-                       f"first {m_out} coefficients of each; samples = input samples"}
+                       f"first {m_out} coefficients of each; samples = input samples",
+           "plan_ms": plan_ms}
+    rng = np.random.default_rng(7)
+    sig = np.sort(rng.choice(batch, 8, replace=False))
+    ops = [cauchy.make_plan(n, self_loop_v(n, 0), r) for r in rhos]
 
     def timed(step, bytes_per_step):
         lc = pkg.dctplus_launch_count()
@@ -368,15 +535,34 @@ def bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak, n=512, batch=16
         launches = pkg.dctplus_launch_count() - lc
         times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
         t_ms = float(np.mean(times))
+        recs = trace_kernels(pkg, torch, stream, step, flush)
         return {"value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t_ms,
                 "launches_per_step": launches,
-                "hbm_frac_of_measured": bytes_per_step / (t_ms * 1e-3) / 1e9 / hbm_peak}
+                "hbm_frac_of_measured": bytes_per_step / (t_ms * 1e-3) / 1e9 / hbm_peak,
+                "roofline": roofline_of(recs, hbm_peak, bf16_peak, peak_src)}
 
     handles = [p.handle for p in plans]
     algo_bytes = 4.0 * batch * (n + width)
     for c_p, name in ((n, "pruned_exact"), (m_out, "pruned_truncated_cp")):
-        out[name] = timed(lambda c_p=c_p: pkg.dctplus_execute_pruned(
-            handles, x.data_ptr(), n, y.data_ptr(), width, batch, m_out, c_p, sh), algo_bytes)
+        def step(c_p=c_p):
+            pkg.dctplus_execute_pruned(handles, x.data_ptr(), n, y.data_ptr(), width, batch, m_out,
+                                       c_p, sh)
+        out[name] = timed(step, algo_bytes)
+        step()
+        torch.cuda.synchronize()
+        got = y.cpu().numpy()[sig].astype(np.float64)
+        err, bound_ok = 0.0, True
+        for k, op in enumerate(ops):
+            part = got[:, k * m_out:(k + 1) * m_out]
+            if c_p == n:  # exact first m_out coefficients
+                ref = cauchy.transform(op, xh[sig], rows=np.arange(m_out))
+            else:  # Theorem 3.4's truncated block
+                ref = cauchy.pruned_transform(op, xh[sig], m_out, c_p)
+            err = max(err, float((np.abs(part - ref).max(axis=1) / np.linalg.norm(xh[sig], axis=1)).max()))
+        out[name]["fp32_err_vs_fp64_oracle"] = {
+            "max_abs_rel_to_signal_norm": err,
+            "sample": f"{len(sig)} signals x {m_out} coefficients x {len(ops)} updates"
+                      + ("" if c_p == n else "; against the oracle's Theorem 3.4 truncated block")}
 
     def full():
         for p, yy in zip(plans, ys):
@@ -387,14 +573,20 @@ def bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak, n=512, batch=16
     return out
 
 
-def bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak, n=1024, batch=8192):
+def bench_backward(pkg, torch, dev, stream, args, flush, peaks, n=1024, batch=8192):
     """Differentiable transform: n = 1024, batch 8192, loss = sum of squared coefficients
     512..1023, dense unit v (seed 1), rho = 2.0. One step = forward + backward to x, rho and v
     (the loss gradient 2 y on the upper half is formed on the device by torch, not timed as
     transform work but inside the step)."""
+    from oracle import cauchy, gradient
     from synthetic import normal_signals, random_unit_v
-    plan = pkg.Plan(n, random_unit_v(n), 2.0)
-    x = torch.tensor(normal_signals(batch, n, seed=0), dtype=torch.float32, device=dev)
+    hbm_peak, bf16_peak, peak_src = peaks
+    v = random_unit_v(n)
+    t0 = time.perf_counter()
+    plan = pkg.Plan(n, v, 2.0)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    xh = normal_signals(batch, n, seed=0)
+    x = torch.tensor(xh, dtype=torch.float32, device=dev)
     y = torch.empty_like(x)
     g = torch.zeros_like(x)
     gx = torch.empty_like(x)
@@ -416,11 +608,29 @@ def bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak, n=1024, batch
     launches = pkg.dctplus_launch_count() - lc
     times, _ = time_graph(step, stream, args.steps, args.warmup, flush)
     t_ms = float(np.mean(times))
+    recs = trace_kernels(pkg, torch, stream, step, flush)
+    step()
+    torch.cuda.synchronize()
+    op = cauchy.make_plan(n, v, 2.0)
+    gh = g.double().cpu().numpy()
+    rng = np.random.default_rng(7)
+    sig = np.sort(rng.choice(batch, 8, replace=False))
+    ref_x = gradient.backward_x(op, gh[sig])
+    gxh = gx.double().cpu().numpy()[sig]
+    r_rho, r_v = gradient.parameter_gradients(op, xh, gh)
+    err = {"gx_normwise_rel_max": float((np.linalg.norm(gxh - ref_x, axis=1)
+                                         / np.linalg.norm(ref_x, axis=1)).max()),
+           "grad_rho_rel": abs(float(g_rho.item()) - r_rho) / abs(r_rho),
+           "grad_v_rel": float(np.linalg.norm(g_v.cpu().numpy() - r_v) / np.linalg.norm(r_v)),
+           "sample": "gx on 8 signals; grad_rho and grad_v over the whole batch (the oracle's "
+                     "gradients for the same upstream g)"}
     plan.close()
     return {"workload": f"n={n}, batch {batch}, loss = sum y[:, {n // 2}:]^2, dense unit v (seed 1), "
                         "rho = 2.0; forward + backward to x, rho, v",
             "value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s (forward + backward)",
-            "ms_per_step": t_ms, "launches_per_step": launches}
+            "ms_per_step": t_ms, "launches_per_step": launches, "plan_ms": plan_ms,
+            "roofline": roofline_of(recs, hbm_peak, bf16_peak, peak_src),
+            "fp32_err_vs_fp64_oracle": err}
 
 
 def bench_dense_gft(pkg, torch, dev, stream, args, flush, wl, plans, seg):
@@ -524,9 +734,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true", help="skip the n=1024 and comparator items")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the CPU oracle baseline and the oracle error checks of the extra lines")
     ap.add_argument("--quick", action="store_true", help="only the n=1024 large-n item")
-    ap.add_argument("--only", choices=["n256", "n1024", "n4096", "n16384", "pruned", "backward"],
+    ap.add_argument("--only", choices=["n256", "n1024", "n4096", "n16384", "pruned", "backward", "fp64"],
                     help="run just this secondary line (for profiling one kernel family); prints "
                          "its JSON object alone")
     args = ap.parse_args()
@@ -546,7 +757,7 @@ def run_only(args):
     import paper_2409_08970_gb300 as pkg
     from paper_2409_08970_gb300 import build as _build
     _build.build()
-    hbm_peak, _, _ = load_peaks()
+    peaks = load_peaks()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -559,11 +770,13 @@ def run_only(args):
              "n4096": (4096, 4096, [H, D, G]), "n16384": (16384, 512, [H])}
     if args.only in large:
         n, batch, modes = large[args.only]
-        out = bench_large(pkg, torch, dev, stream, args, flush, hbm_peak, n, batch, modes)
+        out = bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, not args.no_cpu)
     elif args.only == "pruned":
-        out = bench_pruned(pkg, torch, dev, stream, args, flush, hbm_peak)
+        out = bench_pruned(pkg, torch, dev, stream, args, flush, peaks)
+    elif args.only == "fp64":
+        out = bench_fp64_n64(pkg, torch, dev, stream, args, flush, peaks)
     else:
-        out = bench_backward(pkg, torch, dev, stream, args, flush, hbm_peak)
+        out = bench_backward(pkg, torch, dev, stream, args, flush, peaks)
     print(json.dumps({args.only: out}), flush=True)
 
 

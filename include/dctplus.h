@@ -162,20 +162,26 @@ dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const v
 dctplus_status dctplus_execute_host(dctplus_plan_t plan, dctplus_dtype dtype, const void* x_host,
                                     void* y_host, int64_t batch, dctplus_stream_t stream);
 
-/* Same FP32 forward transform (Algorithm 1 steps 1-2, then Theorem 3.1's
- * Cauchy product on the CUDA cores) for callers that cannot let the library
- * allocate device memory while it executes. The paper has no counterpart:
- * this is an execution variant only, with the same results as dctplus_execute
- * up to FP32 rounding.
- *   - Allocates nothing. The DCT-II coefficients go to a scratch array of
- *     2^22 floats (16 MiB) compiled into the library's device image.
+/* Same FP32 forward transform as dctplus_execute, for callers that cannot let
+ * the library allocate device memory while it executes (an allocation may
+ * synchronise the whole device and stall a latency-bound serving loop, and
+ * some hosts hand all device memory to their own pool up front). The paper has
+ * no counterpart: this is an execution variant only, with the same results as
+ * dctplus_execute up to FP32 rounding.
+ *   - Allocates nothing at execute time. The DCT-II coefficients go to a
+ *     scratch array of 2^22 floats (16 MiB) compiled into the library's
+ *     device image, which every GPU that loads it holds until exit.
  *   - Supports plans with n a power of two, 128 <= n <= 16384 (else
- *     UNSUPPORTED), and batch * n <= 2^22 (else SCRATCH_LIMIT, before any
- *     launch).
+ *     UNSUPPORTED), and batch * n <= 2^22 (else SCRATCH_LIMIT); both are
+ *     checked before any launch.
  *   - x_dev, y_dev: FP32 device rows as in dctplus_execute, 4-byte aligned,
  *     ldx, ldy >= n, not overlapping.
  *   - The first call on a device (with the plan's device current) looks up the
- *     scratch address; make that first call before any stream capture begins.
+ *     scratch address. With lazy module loading (the CUDA default) that first
+ *     call also loads the module holding the array, and the driver reserves
+ *     the 16 MiB then: make the first call during set-up, before any stream
+ *     capture begins. The address is cached per device and context; a call in
+ *     a new context (e.g. after cudaDeviceReset) looks it up again.
  *   - The scratch need not start at zero; each call writes all it reads.
  *   - All calls on one device share the scratch: calls that may run at the
  *     same time (other streams or threads, unordered) race on it and must be
@@ -287,6 +293,24 @@ dctplus_status dctplus_sync_check(dctplus_stream_t stream);
 
 /* Number of kernels this library has launched in this process (all devices). */
 int64_t dctplus_launch_count(void);
+
+/* Kernel timing trace, a measurement aid with no counterpart in the paper.
+ * dctplus_trace_begin records a start event on `stream`; until
+ * dctplus_trace_end, every kernel an execute, pruned or backward call launches
+ * on that stream is followed by an event. dctplus_trace_end synchronises the
+ * stream and reports, for the first `cap` launches in order, the kernel's name
+ * (a static string), its device time in ms (from the previous event, so a
+ * launch's time includes any gap before it), and its algorithmic work: bytes
+ * of global memory it must move (inputs read once, outputs written once) and
+ * flops (tensor-core products counted as executed, the three products of a
+ * split operand included). Any output array may be NULL. Returns the number of
+ * launches traced, or -1 (no trace open on `stream`, or a CUDA error). One
+ * trace at a time per process; begin fails with INVALID_ARG while one is open
+ * or while `stream` is capturing, and launches issued during a capture are not
+ * traced. Meant for profiling runs, not for the timed region of a benchmark. */
+dctplus_status dctplus_trace_begin(dctplus_stream_t stream);
+int dctplus_trace_end(dctplus_stream_t stream, const char** names, float* ms, double* bytes,
+                      double* flops, int cap);
 
 const char* dctplus_status_string(dctplus_status status);
 

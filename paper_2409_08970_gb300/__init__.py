@@ -9,6 +9,8 @@ CUDA kernels, and there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import weakref
+from collections import OrderedDict
 
 import numpy as np
 
@@ -25,7 +27,8 @@ __all__ = [
     "dctplus_execute", "dctplus_execute_host", "dctplus_execute_noalloc", "dctplus_execute_pruned",
     "dctplus_backward", "dctplus_group_create", "DctPlusFunction", "dct_plus", "dctplus_group_destroy",
     "dctplus_execute_group", "dctplus_execute_group_host", "dctplus_sync_check",
-    "dctplus_launch_count", "dctplus_status_string", "library_path",
+    "dctplus_launch_count", "dctplus_status_string", "dctplus_trace_begin", "dctplus_trace_end",
+    "library_path",
 ]
 
 
@@ -140,6 +143,22 @@ def dctplus_execute_group_host(g, x_ptr: int, y_ptr: int, total_elems: int, seg:
 
 def dctplus_sync_check(stream: int = 0) -> int:
     return int(_lib.load().dctplus_sync_check(stream))
+
+
+def dctplus_trace_begin(stream: int) -> None:
+    check(_lib.load().dctplus_trace_begin(stream), "dctplus_trace_begin")
+
+
+def dctplus_trace_end(stream: int, cap: int = 256) -> list:
+    """Per traced launch: (kernel name, device ms, algorithmic bytes, flops)."""
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_float * cap)()
+    by = (ctypes.c_double * cap)()
+    fl = (ctypes.c_double * cap)()
+    cnt = _lib.load().dctplus_trace_end(stream, names, ms, by, fl, cap)
+    if cnt < 0:
+        raise DctPlusError(_lib.ERR_INVALID_ARG, "dctplus_trace_end")
+    return [(names[i].decode(), float(ms[i]), float(by[i]), float(fl[i])) for i in range(min(cnt, cap))]
 
 
 # ---------------------------------------------------------------- wrappers
@@ -257,17 +276,49 @@ class Group:
 
 # ---------------------------------------------------------------- autograd
 
-_plan_cache: dict = {}
+# Plans of the autograd function, least recently used first, keyed by the values of
+# (n, v, rho, device). Evicting a plan only drops the cache's reference: a forward whose
+# backward is still pending keeps its plan alive through ctx.plan, and the plan's
+# device tables are freed when the last reference goes (Plan.__del__).
+_PLAN_CACHE_MAX = 16
+_plan_cache: "OrderedDict[tuple, Plan]" = OrderedDict()
+# Per tensor object: (weak reference, version counter, value key). When the same v
+# (or rho) tensor comes back unmodified, its value key is reused without copying the
+# tensor to the host again.
+_value_keys: dict = {}
 
 
-def _cached_plan(n: int, v_host: np.ndarray, rho: float, device: int) -> "Plan":
-    key = (n, v_host.tobytes(), float(rho), device)
+def _value_key(t, to_host):
+    """Host value of tensor ``t`` as a hashable key, memoised while ``t`` is unmodified."""
+    import torch
+    if not torch.is_tensor(t):
+        return to_host(t)
+    memo = _value_keys.get(id(t))
+    if memo is not None and memo[0]() is t and memo[1] == t._version:
+        return memo[2]
+    key = to_host(t)
+    if len(_value_keys) > 4 * _PLAN_CACHE_MAX:  # drop entries of tensors that are gone
+        for k in [k for k, m in _value_keys.items() if m[0]() is None]:
+            del _value_keys[k]
+    _value_keys[id(t)] = (weakref.ref(t), t._version, key)
+    return key
+
+
+def _cached_plan(n: int, v, rho, device: int) -> "Plan":
+    import torch
+    v_key = _value_key(v, lambda t: np.ascontiguousarray(
+        t.detach().to("cpu", torch.float64).numpy() if torch.is_tensor(t) else t,
+        dtype=np.float64).tobytes())
+    rho_key = _value_key(rho, lambda t: float(t))
+    key = (n, v_key, rho_key, device)
     plan = _plan_cache.get(key)
-    if plan is None:
-        if len(_plan_cache) >= 16:
-            _plan_cache.pop(next(iter(_plan_cache))).close()
-        plan = Plan(n, v_host, float(rho), device=device)
-        _plan_cache[key] = plan
+    if plan is not None:
+        _plan_cache.move_to_end(key)
+        return plan
+    while len(_plan_cache) >= _PLAN_CACHE_MAX:
+        _plan_cache.popitem(last=False)  # no close(): pending backwards may still hold it
+    plan = Plan(n, np.frombuffer(v_key, dtype=np.float64), rho_key, device=device)
+    _plan_cache[key] = plan
     return plan
 
 
@@ -278,12 +329,13 @@ def _make_function():
         """y = X(v, rho)^T x on float32 CUDA signals (rows of x), differentiable in x, v and rho.
 
         v (n,) and rho (scalar) are float64 tensors; the plan for (v, rho) is built on the GPU
-        (and cached) in the forward. The backward calls dctplus_backward."""
+        (and cached, least recently used out) in the forward, and held by ctx until the
+        backward, which calls dctplus_backward. The same unmodified v tensor is not copied
+        to the host again."""
 
         @staticmethod
         def forward(ctx, x, v, rho):
-            v_host = v.detach().to("cpu", torch.float64).numpy()
-            plan = _cached_plan(x.shape[1], v_host, float(rho), x.device.index or 0)
+            plan = _cached_plan(x.shape[1], v, rho, x.device.index or 0)
             y = plan.forward(x.contiguous())
             ctx.plan = plan
             ctx.save_for_backward(y)

@@ -40,7 +40,7 @@ EXPORTS = (
     "dctplus_execute_noalloc", "dctplus_execute_pruned", "dctplus_backward",
     "dctplus_group_create", "dctplus_group_destroy", "dctplus_execute_group",
     "dctplus_execute_group_host", "dctplus_sync_check", "dctplus_launch_count",
-    "dctplus_status_string",
+    "dctplus_status_string", "dctplus_trace_begin", "dctplus_trace_end",
 )
 
 
@@ -86,6 +86,8 @@ def load():
         "dctplus_sync_check": (c_int, [vp]),
         "dctplus_launch_count": (i64, []),
         "dctplus_status_string": (ctypes.c_char_p, [c_int]),
+        "dctplus_trace_begin": (c_int, [vp]),
+        "dctplus_trace_end": (c_int, [vp, vp, vp, vp, vp, c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

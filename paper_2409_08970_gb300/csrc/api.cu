@@ -176,6 +176,48 @@ static dctplus_status group_host_pipelined(dctplus_group_t g, const float* x_hos
 
 }  // namespace dctplus
 
+// ------------------------------------------------------------ kernel trace
+
+namespace dctplus {
+
+struct TraceRec {
+    const char* name;
+    double bytes, flops;
+    cudaEvent_t ev;
+};
+
+static std::mutex g_trace_mu;
+static cudaStream_t g_trace_stream = nullptr;
+static bool g_trace_on = false;
+static cudaEvent_t g_trace_start = nullptr;
+static std::vector<TraceRec> g_trace;
+static std::vector<cudaEvent_t> g_trace_pool;
+
+static cudaEvent_t trace_event() {
+    if (!g_trace_pool.empty()) {
+        cudaEvent_t e = g_trace_pool.back();
+        g_trace_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void note_launch(cudaStream_t s, const char* name, double bytes, double flops) {
+    count_launch();
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (!g_trace_on || s != g_trace_stream) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    cudaEvent_t e = trace_event();
+    if (!e) return;
+    cudaEventRecord(e, s);
+    g_trace.push_back({name, bytes, flops, e});
+}
+
+}  // namespace dctplus
+
 using namespace dctplus;
 
 extern "C" {
@@ -197,6 +239,46 @@ const char* dctplus_status_string(dctplus_status s) {
 }
 
 int64_t dctplus_launch_count(void) { return g_launches.load(); }
+
+
+dctplus_status dctplus_trace_begin(dctplus_stream_t stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (g_trace_on) return DCTPLUS_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DCTPLUS_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return DCTPLUS_ERR_INVALID_ARG;
+    if (!g_trace_start) DCTPLUS_CUDA_TRY(cudaEventCreate(&g_trace_start));
+    DCTPLUS_CUDA_TRY(cudaEventRecord(g_trace_start, s));
+    g_trace_stream = s;
+    g_trace_on = true;
+    return DCTPLUS_OK;
+}
+
+int dctplus_trace_end(dctplus_stream_t stream, const char** names, float* ms, double* bytes,
+                      double* flops, int cap) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (!g_trace_on || s != g_trace_stream) return -1;
+    g_trace_on = false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    const int cnt = (int)g_trace.size();
+    cudaEvent_t prev = g_trace_start;
+    for (int i = 0; i < cnt; ++i) {
+        if (i < cap) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, prev, g_trace[i].ev) != cudaSuccess) t = -1.f;
+            if (names) names[i] = g_trace[i].name;
+            if (ms) ms[i] = t;
+            if (bytes) bytes[i] = g_trace[i].bytes;
+            if (flops) flops[i] = g_trace[i].flops;
+        }
+        prev = g_trace[i].ev;
+    }
+    for (auto& r : g_trace) g_trace_pool.push_back(r.ev);
+    g_trace.clear();
+    return cnt;
+}
 
 dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, double rho,
                             const dctplus_opts* opts) {

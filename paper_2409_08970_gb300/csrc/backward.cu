@@ -283,7 +283,7 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
         float* g_lo = ws + plane;
         if (tc_shape && aligned16(gy, ldg)) {
             k_lo_rows<<<blocks_for(plane), 256, 0, st>>>(gy, ldg, n, batch, g_lo);
-            count_launch();
+            note_launch(st, "k_lo_rows", 8.0 * plane, 0.0);
             DCTPLUS_CUDA_TRY(cudaGetLastError());
             rc = launch_gemm_tc(gy, g_lo, ldg, T->wt_hi, T->wt_lo, n, t, n, (int)batch, n, n, st, cur);
         } else {
@@ -307,7 +307,7 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
     DCTPLUS_CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * (n + n + 2), st));
     k_param_prep<<<blocks_for(plane), 256, 0, st>>>(y, ldy, gy, ldg, T->w32, n, batch, a_hi,
                                                     tc ? a_lo : nullptr);
-    count_launch();
+    note_launch(st, "k_param_prep", (tc ? 24.0 : 16.0) * plane, 2.0 * plane);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     rc = tc ? launch_gemm_tc(a_hi, a_lo, n, T->k_hi, T->k_lo, n, pq, n, (int)(2 * batch), n, n, st, cur)
             : launch_rows_gemm(a_hi, n, T->k32, n, pq, n, 2 * batch, n, n, st);
@@ -315,22 +315,22 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
     dim3 grid((n + 255) / 256, (unsigned)((batch + kRedRows - 1) / kRedRows));
     if (grid.y > 65535) return DCTPLUS_ERR_UNSUPPORTED;
     k_param_reduce<<<grid, 256, 0, st>>>(y, ldy, gy, ldg, T->w32, pq, n, batch, rsum, grho_out);
-    count_launch();
+    note_launch(st, "k_param_reduce", 16.0 * plane, 6.0 * plane);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     if (grad_v) {  // rho X rsum = rho U (W^T rsum): W^T from its hi / lo table, FP64 sums
         float* t32 = reinterpret_cast<float*>(grho + 2);  // n floats after the FP64 scratch
         float* v32 = t32 + n;
         k_table_apply<<<(n + 7) / 8, 256, 0, st>>>(n, T->wt_hi, T->wt_lo, rsum, 1.0, t64, t32);
-        count_launch();
+        note_launch(st, "k_table_apply", 8.0 * (double)n * n, 4.0 * (double)n * n);
         DCTPLUS_CUDA_TRY(cudaGetLastError());
         if (fft) {  // DCT-III of the single vector in FP32, scaled by rho into FP64
             rc = launch_idct_fft(p, t32, n, v32, n, 1, st);
             if (rc != DCTPLUS_OK) return rc;
             k_scale_f32_to_f64<<<(n + 255) / 256, 256, 0, st>>>(n, v32, p->rho, grad_v);
-            count_launch();
+            note_launch(st, "k_scale_f32_to_f64", 12.0 * n, (double)n);
         } else {
             k_table_apply<<<(n + 7) / 8, 256, 0, st>>>(n, T->u32, nullptr, t64, p->rho, grad_v, nullptr);
-            count_launch();
+            note_launch(st, "k_table_apply", 4.0 * (double)n * n, 2.0 * (double)n * n);
         }
         DCTPLUS_CUDA_TRY(cudaGetLastError());
     }

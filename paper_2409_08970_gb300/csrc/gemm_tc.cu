@@ -283,7 +283,10 @@ dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int grid = std::min(P.tiles_m * P.tiles_n, std::max(sms, 1));
     gemm::k_gemm_tc<<<grid, gemm::kThreads, gemm::kSmemBytes, s>>>(P);
-    count_launch();
+    // A hi and lo read once over the columns the tiles use, B hi and lo once, Y written
+    note_launch(s, "k_gemm_tc", 8.0 * (double)M * std::min(Ka, K + (P.tiles_n - 1) * gemm::kBN) +
+                                   8.0 * (double)N * K + 4.0 * (double)M * N,
+                6.0 * (double)M * N * K);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }

@@ -442,7 +442,7 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     }
     k_p2m<<<dim3((unsigned)((batch + 31) / 32), (unsigned)((h->nleaf + 7) / 8)), 256, p2m_smem, st>>>(
         h->nleaf, h->zf, h->tq, s_hi, n, batch, mc, mc_lo, h->ncp, n, h->nout, h->out_w, po);
-    count_launch();
+    note_launch(st, "k_p2m", 4.0 * plane + 8.0 * cplane + 4.0 * pplane, 2.0 * kR * plane);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     r = launch_gemm_tc_band(mc, mc_lo, h->ncp, h->nc, h->kf_hi, h->kf_lo, h->ncp, lc, h->ncp,
                             (int)batch, h->ncp, h->ncp, nullptr, st, p->device);
@@ -455,7 +455,7 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     k_l2p<<<dim3((unsigned)((batch + kL2pSig - 1) / kL2pSig), (unsigned)(n / 256 + (h->nout > 0))), 256, 0, st>>>(
         n, h->wl, h->row_leaf, h->pna, lc, h->ncp, y, ldy, batch, h->nleaf,
         h->nout > 0 ? h->out_row[0] : -1, h->nout > 1 ? h->out_row[1] : -1, po);
-    count_launch();
+    note_launch(st, "k_l2p", 8.0 * plane + 4.0 * cplane + 4.0 * pplane, 2.0 * kR * plane);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }

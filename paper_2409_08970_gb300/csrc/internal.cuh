@@ -15,6 +15,7 @@ constexpr int kMaxN = 16384;
 constexpr int kSmallMax = 64;      // n <= 64: fused small-n kernels
 constexpr int kTableMax = 4096;    // n <= 4096: a stored FP32 Cauchy table is allowed
 constexpr int kF64Max = 1024;      // FP64 execute path
+constexpr int kCauchySimtSigTile = 64;  // signals per CTA tile of the CUDA-core Cauchy product
 
 // Device error word bits (dctplus_sync_check).
 constexpr unsigned kErrIndex = 1u;    // an index guard fired
@@ -24,6 +25,14 @@ extern std::atomic<int64_t> g_launches;
 
 // Every kernel launch goes through this so dctplus_launch_count is exact.
 inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Execute-path launches also report themselves for the kernel timing trace
+// (dctplus_trace_begin / dctplus_trace_end): `name` is the kernel, `bytes` the
+// algorithmic global-memory traffic of the launch (inputs read once, outputs
+// written once), `flops` its arithmetic (tensor-core products counted as
+// executed, split operands included). When a trace is open on stream s and s is
+// not capturing, an event is recorded after the launch. Always counts it.
+void note_launch(cudaStream_t s, const char* name, double bytes, double flops);
 
 unsigned* device_error_word(int device);  // lazily allocated per device
 

@@ -85,6 +85,10 @@ dctplus_status setup_large(dctplus_plan_t p) {
 
 // ------------------------------------------------------------------ DCT-II
 
+// arithmetic of a DCT-II / DCT-III of length n through a complex FFT of n / 2:
+// about 2.5 n log2 n real operations
+static double dct_flops(int n) { return 2.5 * n * std::log2((double)n); }
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -396,7 +400,7 @@ static dctplus_status launch_r8(int n, const float* x, int64_t ldx, float* s_out
         }
     }
     k_dct_r8<M><<<(unsigned)grid, spc * (M / 8), smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec);
-    count_launch();
+    note_launch(st, "k_dct_r8", (s_lo ? 12.0 : 8.0) * batch * n, dct_flops(n) * batch);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
@@ -495,7 +499,7 @@ static dctplus_status launch_ir8(int n, const float* s, int64_t lds, float* x, i
         }
     }
     k_idct_r8<M><<<(unsigned)grid, spc * (M / 8), smem, st>>>(n, s, lds, x, ldx, batch, tw, vec);
-    count_launch();
+    note_launch(st, "k_idct_r8", 8.0 * batch * n, dct_flops(n) * batch);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
@@ -552,7 +556,7 @@ dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, flo
     k_dct_fft<<<(unsigned)grid, threads, smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch,
                                                      reinterpret_cast<const float2*>(p->d_twiddle),
                                                      vec);
-    count_launch();
+    note_launch(st, "k_dct_fft", (s_lo ? 12.0 : 8.0) * batch * n, dct_flops(n) * batch);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
@@ -575,7 +579,7 @@ __device__ __forceinline__ float gen_w(int k, int pole, float tau, float na, con
     return na * zk / (tau - d);      // -a_r z_k / (mu_r - lambda_k)
 }
 
-constexpr int kGB = 64;  // signals per tile
+constexpr int kGB = kCauchySimtSigTile;  // signals per tile
 constexpr int kGR = 64;  // output rows per tile
 constexpr int kGK = 16;
 
@@ -655,7 +659,7 @@ dctplus_status launch_cauchy_simt(dctplus_plan_t p, const float* s_in, int64_t l
     dim3 grid((n + kGR - 1) / kGR, (unsigned)gy);
     k_cauchy_simt<<<grid, 256, 0, st>>>(n, s_in, lds, y, ldy, batch, p->d_w32, p->d_gen_pole,
                                         p->d_gen_tau, p->d_gen_na, p->d_gen_z, p->d_gen_sin);
-    count_launch();
+    note_launch(st, "k_cauchy_simt", 8.0 * batch * n, 2.0 * (double)batch * n * n);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
@@ -699,7 +703,7 @@ dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, 
     int64_t grid = std::min<int64_t>(batch, 152 * 8);
     k_dense_f64<<<(unsigned)grid, 256, sizeof(double) * 2 * p->n, st>>>(p->n, x, ldx, y, ldy, batch,
                                                                         p->d_ct64, p->d_w64);
-    count_launch();
+    note_launch(st, "k_dense_f64", 16.0 * batch * p->n, 4.0 * (double)batch * p->n * p->n);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
@@ -740,7 +744,7 @@ dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, f
         if (!ws) return DCTPLUS_ERR_CUDA;
         int64_t blocks = std::min<int64_t>((int64_t)((plane + 255) / 256), 152 * 16);
         k_split_rows<<<(unsigned)blocks, 256, 0, st>>>(x, ldx, n, batch, x_ok ? nullptr : ws, ws + plane);
-        count_launch();
+        note_launch(st, "k_split_rows", (x_ok ? 8.0 : 12.0) * plane, 0.0);
         DCTPLUS_CUDA_TRY(cudaGetLastError());
         return launch_gemm_tc(x_ok ? x : ws, ws + plane, x_ok ? ldx : n, p->d_xthi, p->d_xtlo, n, y,
                               ldy, (int)batch, n, n, st, p->device);

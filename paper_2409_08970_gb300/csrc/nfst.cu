@@ -170,7 +170,7 @@ dctplus_status launch_nfst(dctplus_plan_t p, const T* x, int64_t ldx, T* y, int6
                                                            p->d_nfst_znd, p->d_nfst_kind,
                                                            reinterpret_cast<const NfstRow*>(p->d_nfst_rows),
                                                            p->d_row_pole, p->d_row_tau, p->d_row_a);
-    count_launch();
+    note_launch(st, "k_nfst_route", 2.0 * sizeof(T) * (double)batch * n, 6.0 * (double)batch * n * n);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }

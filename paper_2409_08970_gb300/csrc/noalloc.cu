@@ -1,8 +1,8 @@
-// dctplus_execute_noalloc: the large-n FP32 forward transform (Algorithm 1
-// steps 1-2 as the DCT-II, then the Cauchy product of Theorem 3.1 on the CUDA
-// cores) with its intermediate DCT-II coefficients held in a fixed scratch
-// array compiled into this translation unit instead of a workspace allocated
-// on demand.
+// dctplus_execute_noalloc: the large-n FP32 forward transform (the DCT-II
+// kernel, then the CUDA-core Cauchy product) with its intermediate DCT-II
+// coefficients held in a fixed scratch array compiled into this translation
+// unit instead of a workspace allocated on demand. The paper has no
+// counterpart; this is an execution variant of dctplus_execute.
 //
 // Who needs it: a caller that cannot let the library allocate device memory
 // while it executes. cudaMalloc and cudaFree may synchronise the whole device,
@@ -12,10 +12,14 @@
 // dctplus_execute grows a per-(plan, stream) workspace on first use, which
 // such callers cannot accept.
 //
-// Set-up: the first call on a device, with that device current, looks up the
-// device address of the scratch array (cudaGetSymbolAddress) and caches it per
-// device. That first call must come before any stream capture begins. Later
-// calls only read the cache.
+// Set-up: the first call on a device (in a given CUDA context), with that
+// device current, looks up the device address of the scratch array
+// (cudaGetSymbolAddress) and caches it with the context it belongs to. With
+// lazy module loading (the CUDA default) that first lookup is also what loads
+// this file's module, and the driver reserves the 16 MiB array at that moment;
+// so the first call belongs in the caller's set-up, before any stream capture
+// begins. A later call in another context (after cudaDeviceReset, say) looks
+// the address up again instead of reusing one from a destroyed context.
 //
 // Nothing in the scratch has to start at zero: the DCT kernel writes every
 // coefficient the Cauchy kernel then reads, within the same call.
@@ -24,6 +28,8 @@
 // overlaps in time (different streams, or different host threads, without an
 // ordering between them) overwrite each other's coefficients; callers must
 // order them, e.g. by issuing them on one stream.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -31,20 +37,44 @@
 namespace dctplus {
 
 constexpr int64_t kNoAllocMaxSamples = int64_t(1) << 22;  // batch * n limit (16 MiB of FP32)
+constexpr int kNoAllocMaxN = kMaxN;
+// the Cauchy product's grid.y (batch / 64 signal tiles) can never exceed its limit here
+static_assert(kNoAllocMaxSamples / 128 / kCauchySimtSigTile <= 65535, "Cauchy grid limit");
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocMaxSamples];
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+static CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    });
+    return fn;
+}
+
 static std::mutex g_noalloc_mu;
 static float* g_noalloc_ptr[64] = {};
+static CUcontext g_noalloc_ctx[64] = {};
 
-// Device address of the scratch array on `device` (which must be current).
+// Device address of the scratch array on `device` (which must be current), for
+// the current context.
 static dctplus_status noalloc_scratch(int device, float** out) {
+    CtxGetCurrentFn get_ctx = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return DCTPLUS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    if (!g_noalloc_ptr[device] || g_noalloc_ctx[device] != ctx) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) return DCTPLUS_ERR_CUDA;
         g_noalloc_ptr[device] = static_cast<float*>(ptr);
+        g_noalloc_ctx[device] = ctx;
     }
     *out = g_noalloc_ptr[device];
     return DCTPLUS_OK;
@@ -67,7 +97,12 @@ extern "C" dctplus_status dctplus_execute_noalloc(dctplus_plan_t p, const float*
     const uintptr_t xe = xa + 4 * (size_t)((batch - 1) * ldx + n);
     const uintptr_t ye = ya + 4 * (size_t)((batch - 1) * ldy + n);
     if (xa < ye && ya < xe) return DCTPLUS_ERR_INVALID_ARG;
-    if (n <= kSmallMax || (n & (n - 1)) || !p->d_twiddle) return DCTPLUS_ERR_UNSUPPORTED;
+    // every precondition of both launches is checked here, before the DCT kernel is
+    // queued to write the shared scratch: n a power of two in [128, 16384] (also a
+    // multiple of the Cauchy product's K step) and, through the sample limit, at most
+    // 2^22 / 128 / 64 signal tiles in the Cauchy grid (static_assert above)
+    if (n <= kSmallMax || n > kNoAllocMaxN || (n & (n - 1)) || !p->d_twiddle)
+        return DCTPLUS_ERR_UNSUPPORTED;
     if (batch > kNoAllocMaxSamples / n) return DCTPLUS_ERR_SCRATCH_LIMIT;
     int cur = -1;
     if (cudaGetDevice(&cur) != cudaSuccess) return DCTPLUS_ERR_NO_DEVICE;

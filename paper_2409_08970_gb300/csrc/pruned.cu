@@ -200,7 +200,8 @@ dctplus_status launch_rows_gemm(const float* a, int64_t lda, const float* w, int
     }
     dim3 grid((N + kRR - 1) / kRR, (unsigned)by);
     k_rows_gemm<<<grid, 256, 0, st>>>(a, lda, w, ldw, y, ldy, batch, N, Kd);
-    count_launch();
+    note_launch(st, "k_rows_gemm", 4.0 * ((double)batch * (Kd + N) + (double)N * Kd),
+                2.0 * (double)batch * N * Kd);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }

@@ -195,7 +195,8 @@ static int sm_count(int dev) {
 
 template <typename T>
 static dctplus_status launch_small_common(const SmallLaunch& L, const T* x, int64_t ldx, T* y,
-                                          int64_t ldy, cudaStream_t s, int dev) {
+                                          int64_t ldy, cudaStream_t s, int dev, double samples,
+                                          double flops) {
     if (L.ntiles == 0) return DCTPLUS_OK;
     size_t smem = small_smem_bytes<T>();
     static bool attr_set[2][64] = {};
@@ -207,7 +208,8 @@ static dctplus_status launch_small_common(const SmallLaunch& L, const T* x, int6
     int per_sm = sizeof(T) == 4 ? 2 : 1;
     int grid = std::min(L.ntiles, sm_count(dev) * per_sm);
     k_small_simt<T><<<grid, 256, smem, s>>>(L, x, ldx, y, ldy, device_error_word(dev));
-    count_launch();
+    note_launch(s, sizeof(T) == 4 ? "k_small_simt<float>" : "k_small_simt<double>",
+                2.0 * sizeof(T) * samples, flops);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
@@ -226,7 +228,8 @@ static dctplus_status launch_small_single(dctplus_plan_t p, const T* x, int64_t 
     if (nt > INT32_MAX) return DCTPLUS_ERR_UNSUPPORTED;
     L.ntiles = (int)nt;
     L.batch = batch;
-    return launch_small_common<T>(L, x, ldx, y, ldy, s, p->device);
+    const double samples = (double)batch * p->n;
+    return launch_small_common<T>(L, x, ldx, y, ldy, s, p->device, samples, 4.0 * p->n * samples);
 }
 
 dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
@@ -289,7 +292,13 @@ dctplus_status launch_group_simt(dctplus_group_t g, const float* x, float* y, cu
     L.segs = g->d_seg;
     L.tiles = reinterpret_cast<const SmallTile*>(g->d_tiles);
     L.ntiles = g->ntiles;
-    return launch_small_common<float>(L, x, -1, y, -1, s, g->device);
+    double samples = 0.0, flops = 0.0;
+    for (size_t i = 0; i + 2 < g->seg_cache.size(); i += 3) {
+        const double rows_n = (double)g->seg_cache[i + 2] * g->plans[g->seg_cache[i]]->n;
+        samples += rows_n;
+        flops += 4.0 * g->plans[g->seg_cache[i]]->n * rows_n;
+    }
+    return launch_small_common<float>(L, x, -1, y, -1, s, g->device, samples, flops);
 }
 
 }  // namespace dctplus

@@ -568,12 +568,14 @@ dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream
         TcParams P;
         memset(&P, 0, sizeof(P));
         int tiles = 0, ns = 0, tails = 0;
+        double samples = 0.0;
         for (; i0 < segs.size() && ns < kTcMaxSeg; ++i0) {
             const TcSegHost& g = segs[i0];
             const int n = g.plan->n;
             const int64_t rows64 = g.rows * n / 64;
             const int64_t body = rows64 * 64 / n;
             if (g.rows <= 0) continue;
+            samples += (double)g.rows * n;
             if (rows64 > 0 && (!encode_map(&P.xmap[ns], g.x, rows64) || !encode_map(&P.ymap[ns], g.y, rows64)))
                 return DCTPLUS_ERR_CUDA;
             P.images[ns] = g.plan->tc.images;
@@ -598,7 +600,9 @@ dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream
         int grid = std::min(std::max(tiles, tails > 0 ? ns : 0), sm_count_tc(dev));
         if (grid <= 0) continue;
         k_small_tc<<<grid, kTcThreads, kSmemBytes, s>>>(P);
-        count_launch();
+        // executed tensor work per 64-sample packed row: two GEMMs of K = 64, each an
+        // N = 128 (stacked hi | lo) and an N = 64 product: 2 x 192 x 64 multiply-adds
+        note_launch(s, "k_small_tc", 8.0 * samples, 2.0 * 384.0 * samples);
         DCTPLUS_CUDA_TRY(cudaGetLastError());
     }
     return DCTPLUS_OK;

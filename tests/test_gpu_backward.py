@@ -103,6 +103,48 @@ def test_backward_matches_oracle_gradients(pkg, n, batch):
     assert pkg.dctplus_sync_check(0) == 0
 
 
+def test_autograd_many_pending_plans(pkg):
+    """More forwards with distinct rho than the plan cache holds, all before their backwards:
+    every backward must still find its own plan and match the oracle gradients."""
+    n, batch = 64, 20
+    v = random_unit_v(n, seed=3)
+    x = normal_signals(batch, n, seed=11)
+    rhos = [0.1 * (k + 1) for k in range(20)]
+    vt = torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=True)
+    pending = []
+    for rho in rhos:
+        xt = torch.tensor(x, dtype=torch.float32, device="cuda", requires_grad=True)
+        rt = torch.tensor(rho, dtype=torch.float64, device="cuda", requires_grad=True)
+        y = pkg.dct_plus(xt, vt, rt)
+        pending.append((rho, xt, rt, (y[:, n // 2:] ** 2).sum()))
+    assert len(pkg._plan_cache) <= pkg._PLAN_CACHE_MAX
+    for rho, xt, rt, loss in pending:
+        vt.grad = None
+        loss.backward()
+        op = cauchy.make_plan(n, v, rho)
+        g = tail_loss_grad(cauchy.transform(op, x))
+        ref_x = gradient.backward_x(op, g)
+        r_rho, r_v = gradient.parameter_gradients(op, x, g)
+        gx = xt.grad.double().cpu().numpy()
+        assert (np.linalg.norm(gx - ref_x, axis=1) / np.linalg.norm(ref_x, axis=1)).max() < 2e-6, rho
+        assert abs(rt.grad.item() - r_rho) < 1e-3 * abs(r_rho), rho
+        assert np.linalg.norm(vt.grad.cpu().numpy() - r_v) / np.linalg.norm(r_v) < 1e-3, rho
+    # the same unmodified v tensor and rho reuse the cached plan; an in-place change of v
+    # (a new version) makes a new one
+    rt = torch.tensor(0.55, dtype=torch.float64, device="cuda")
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    pkg.dct_plus(xt, vt, rt)
+    before = len(pkg._plan_cache), id(next(reversed(pkg._plan_cache.values())))
+    pkg.dct_plus(xt, vt, rt)
+    assert (len(pkg._plan_cache), id(next(reversed(pkg._plan_cache.values())))) == before
+    with torch.no_grad():
+        vt.mul_(-1.0)
+    y_neg = pkg.dct_plus(xt, vt, rt).double().cpu().numpy()
+    ref = cauchy.transform(cauchy.make_plan(n, -v, 0.55), x)
+    assert (np.linalg.norm(y_neg - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() < 1e-6
+    assert pkg.dctplus_sync_check(0) == 0
+
+
 def test_backward_is_the_adjoint(pkg):
     n, batch = 512, 200
     plan = pkg.Plan(n, random_unit_v(n, seed=3), 0.8)

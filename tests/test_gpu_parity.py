@@ -299,8 +299,9 @@ def test_tensor_core_path_integer_residuals(pkg):
 
 
 def test_tensor_core_path_mixed_exact_and_inexact_tiles(pkg):
-    """Tiles whose samples are all exact in TF32 skip the x_lo product; tiles, row blocks
-    and single rows with inexact samples must not. Mix them inside one launch."""
+    """Tiles whose samples are all exact in TF32 (x_lo = 0) next to tiles, row blocks and
+    single rows with inexact samples, in one launch. The kernel always issues the x_lo
+    product; this guards that a tile's x_lo buffer never leaks into the next tile."""
     n = 16
     rows = 128 * 64 // n * 6 + 37  # six full 128-row tiles of packed rows plus a ragged tail
     x = laplace_residuals(rows * n, seed=3).astype(np.float64).reshape(rows, n)

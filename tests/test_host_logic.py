@@ -1,0 +1,64 @@
+"""Host-side logic that needs no GPU: the benchmark's roofline bookkeeping and oracle-error
+helper, and the value keys of the autograd plan cache."""
+import numpy as np
+import pytest
+
+import bench
+from oracle import cauchy
+from synthetic import normal_signals, random_unit_v
+
+torch = pytest.importorskip("torch")
+
+
+def test_roofline_of_picks_the_dominant_kernel():
+    recs = [{"kernel": "k_dct_r8", "ms": 0.010, "bytes": 8.0e7, "flops": 1e9},
+            {"kernel": "k_gemm_tc", "ms": 0.020, "bytes": 1e7, "flops": 1.0e13},
+            {"kernel": "k_dct_r8", "ms": 0.010, "bytes": 8.0e7, "flops": 1e9},
+            {"kernel": "k_gemm_tc", "ms": 0.030, "bytes": 1e7, "flops": 1.0e13}]
+    r = bench.roofline_of(recs, 6000.0, 2000.0, "measured")
+    assert r["kernel"] == "k_gemm_tc" and r["bound"] == "tensor" and r["launches_of_kernel"] == 2
+    assert r["kernel_ms"] == pytest.approx(0.025)
+    # achieved = flops per launch / mean launch time
+    assert r["achieved"] == pytest.approx(1.0e13 / 25e-6 / 1e12)
+    assert r["peak"] == pytest.approx(2000.0 * 1.1 / 2.25)
+    assert r["share_of_step"] == pytest.approx(0.05 / 0.07)
+    r2 = bench.roofline_of(recs[:1], 6000.0, 2000.0, "measured")
+    assert r2["bound"] == "hbm" and r2["unit"] == "GB/s"
+    assert r2["achieved"] == pytest.approx(8.0e7 / 10e-6 / 1e9)
+    assert r2["frac"] == pytest.approx(r2["achieved"] / 6000.0)
+
+
+def test_oracle_error_is_zero_on_the_oracle_and_sees_a_planted_error():
+    n = 64
+    v = random_unit_v(n)
+    x = normal_signals(20, n, seed=3)
+    y = cauchy.transform(cauchy.make_plan(n, v, 2.0), x)
+    e = bench.oracle_error(n, v, 2.0, x, y)
+    assert e["max_abs"] < 1e-12 and e["normwise_rel_max"] < 1e-12
+    y_bad = y.copy()
+    y_bad[:, 5] += 1e-3
+    e = bench.oracle_error(n, v, 2.0, x, y_bad)
+    assert e["max_abs"] == pytest.approx(1e-3, rel=1e-6)
+    # the sampled-roots form finds the same rows
+    e = bench.oracle_error(n, v, 2.0, x, y, root_sample=10)
+    assert e["max_abs"] < 1e-12 and "sampled" in e["sample"]
+
+
+def test_autograd_value_keys_are_memoised_per_tensor_version():
+    import paper_2409_08970_gb300 as pkg
+    calls = []
+
+    def to_host(t):
+        calls.append(1)
+        return t.detach().numpy().tobytes()
+
+    v = torch.arange(4, dtype=torch.float64)
+    k1 = pkg._value_key(v, to_host)
+    k2 = pkg._value_key(v, to_host)
+    assert k1 == k2 and len(calls) == 1          # same unmodified tensor: no second copy
+    v.add_(1.0)
+    k3 = pkg._value_key(v, to_host)
+    assert k3 != k1 and len(calls) == 2          # in-place change: new version, new key
+    w = v.clone()
+    assert pkg._value_key(w, to_host) == k3 and len(calls) == 3  # equal values, other tensor
+    assert pkg._value_key(1.5, float) == 1.5     # plain numbers are their own key

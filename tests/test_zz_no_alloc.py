@@ -36,16 +36,36 @@ def relerr(y, ref):
     return np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
 
 
-@pytest.mark.parametrize("n,batch", [(128, 300), (1024, 4096), (4096, 64)])
+def oracle_rows(n, v, rho, x, rng):
+    """Sampled oracle rows: all of them up to n = 4096, else about 40 secular-root rows
+    (the sampled set of root numbers mapped to their output rows) and a few deflated rows."""
+    if n <= 4096:
+        return np.arange(n), cauchy.transform(cauchy.make_plan(n, v, rho), x)
+    probe = cauchy.make_plan(n, v, rho, roots=[])
+    K = int(probe.row_kind.sum())
+    roots = np.unique(np.concatenate([rng.choice(K, min(K, 36), replace=False), [0, 1, K - 2, K - 1]]))
+    plan = cauchy.make_plan(n, v, rho, roots=roots)
+    root_rows = np.nonzero((plan.row_kind == 1) & np.isin(plan.row_index, roots))[0]
+    defl = np.nonzero(plan.row_kind == 0)[0][:4]
+    rows = np.sort(np.concatenate([root_rows, defl]))
+    return rows, cauchy.transform(plan, x, rows=rows)
+
+
+# n = 8192 and 16384 have no stored W table: the Cauchy product then generates W tile by
+# tile on the CUDA cores, and n = 16384 takes the generic FFT-DCT kernel (large shared memory)
+@pytest.mark.parametrize("n,batch", [(128, 300), (1024, 4096), (4096, 64), (8192, 512), (16384, 256)])
 def test_noalloc_matches_execute_twice(pkg, n, batch):
+    assert batch * n <= MAX_SAMPLES
     lib = pkg._lib.load()
+    rng = np.random.default_rng(n)
     for v, rho in [(random_unit_v(n), 2.0), (edge_update_v(n, n // 2 - 1, n // 2), -0.5)]:
         plan = pkg.Plan(n, v, rho)
         xh = normal_signals(batch, n, seed=n + 5)
         x = torch.tensor(xh, dtype=torch.float32, device="cuda")
         ref = plan.forward(x).double().cpu().numpy()
-        rows = np.arange(0, batch, max(1, batch // 32))
-        want = cauchy.transform(cauchy.make_plan(n, v, rho), xh[rows])
+        sig = np.arange(0, batch, max(1, batch // (32 if n <= 4096 else 6)))
+        cols, want = oracle_rows(n, v, rho, xh[sig], rng)
+        scale = np.linalg.norm(xh[sig], axis=1)[:, None]
         for call in range(2):
             y = torch.full_like(x, float("nan"))
             free0 = torch.cuda.mem_get_info()[0]
@@ -54,8 +74,12 @@ def test_noalloc_matches_execute_twice(pkg, n, batch):
             if call == 1:  # the first call on the device may have done its one-time set-up
                 assert torch.cuda.mem_get_info()[0] == free0
             got = y.double().cpu().numpy()
+            assert np.isfinite(got).all()
             assert relerr(got, ref).max() < 2 * F32_TOL, (n, rho, call)
-            assert relerr(got[rows], want).max() < F32_TOL, (n, rho, call)
+            if n <= 4096:
+                assert relerr(got[sig], want).max() < F32_TOL, (n, rho, call)
+            else:  # sampled rows: max error relative to the signal's norm
+                assert (np.abs(got[sig][:, cols] - want) / scale).max() < F32_TOL, (n, rho, call)
         plan.close()
     assert pkg.dctplus_sync_check(0) == 0
 
