@@ -145,9 +145,9 @@ int dctplus_plan_cauchy_mode(dctplus_plan_t plan);
  *           x and y must not overlap.
  *   batch : number of signals, >= 0 (0 is a no-op).
  * Scratch: for n >= 128 the plan keeps a device workspace per stream, grown
- * on the first call that needs more: 2 batch n floats (the DCT coefficients
- * and their TF32 remainder); the hierarchical mode adds 3 batch c floats
- * (c = 12 n / 64 rounded up to 128) and batch n / 32 floats. A call that grows
+ * on the first call that needs more: batch n floats (the DCT coefficients);
+ * the hierarchical mode adds batch (2 c + 32) floats (c = 12 n / 64 rounded up
+ * to 128: the leaf moments and the leaf-local coefficients). A call that grows
  * it allocates, so make the first call at the largest batch before capturing
  * the stream into a CUDA graph.
  * Asynchronous on `stream`. Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
@@ -213,7 +213,7 @@ dctplus_status dctplus_execute_noalloc(dctplus_plan_t plan, const float* x_dev, 
  * 2 <= n <= 4096; device pointers 4-byte aligned. The first call for a plan
  * builds its backward tables (W^T and K, 3 x 4 n^2 bytes each; allocates and
  * synchronises, so make it before any stream capture); later calls use the
- * plan's per-stream workspace (6 batch n floats). Asynchronous on `stream`
+ * plan's per-stream workspace (4 batch n floats). Asynchronous on `stream`
  * otherwise. Errors: INVALID_ARG, UNSUPPORTED (n > 4096), NO_DEVICE, CUDA. */
 dctplus_status dctplus_backward(dctplus_plan_t plan, const float* gy_dev, int64_t ldg,
                                 const float* y_dev, int64_t ldy, float* gx_dev, int64_t ldgx,

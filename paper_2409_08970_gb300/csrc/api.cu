@@ -387,8 +387,8 @@ dctplus_status dctplus_execute(dctplus_plan_t p, dctplus_dtype dtype, const void
         if (n > kSmallMax)
             return launch_dense_f64(p, static_cast<const double*>(x_dev), ldx,
                                     static_cast<double*>(y_dev), ldy, batch, s);
-        return launch_small_simt_f64(p, static_cast<const double*>(x_dev), ldx,
-                                     static_cast<double*>(y_dev), ldy, batch, s);
+        return launch_small_f64(p, static_cast<const double*>(x_dev), ldx, static_cast<double*>(y_dev),
+                                ldy, batch, s);
     }
     const float* x = static_cast<const float*>(x_dev);
     float* y = static_cast<float*>(y_dev);

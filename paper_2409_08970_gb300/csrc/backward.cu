@@ -60,10 +60,6 @@ std::mutex g_bwd_mu;
 
 __device__ __forceinline__ float tf32_rn(float v) { return __uint_as_float(ptx::cvt_rna_tf32(v)); }
 
-__device__ __forceinline__ float tf32_lo(float v) {
-    return __uint_as_float(ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu)));
-}
-
 // lambda_a - lambda_b = 4 sin(pi (a + b) / 2n) sin(pi (a - b) / 2n), from the table sin(pi m / 2n)
 __device__ __forceinline__ double pole_gap(int a, int b, int n, const double* S) {
     int m = a + b;
@@ -142,21 +138,10 @@ dctplus_status ensure_tables(dctplus_plan_t p) {
     return DCTPLUS_OK;
 }
 
-// TF32 remainder of rows (the lo operand of a split-TF32 product whose hi operand is the FP32 data)
-__global__ void k_lo_rows(const float* __restrict__ x, int64_t ldx, int n, int64_t batch,
-                          float* __restrict__ lo) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < batch * n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = e / n;
-        const int j = (int)(e - b * n);
-        lo[e] = tf32_lo(x[b * ldx + j]);
-    }
-}
-
-// rows [y * w; g * w] (2 batch x n) and their TF32 remainders
+// rows [y * w; g * w] (2 batch x n)
 __global__ void k_param_prep(const float* __restrict__ y, int64_t ldy, const float* __restrict__ g,
                              int64_t ldg, const float* __restrict__ w, int n, int64_t batch,
-                             float* __restrict__ a_hi, float* __restrict__ a_lo) {
+                             float* __restrict__ a_hi) {
     const int64_t plane = batch * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -165,10 +150,6 @@ __global__ void k_param_prep(const float* __restrict__ y, int64_t ldy, const flo
         const float u = y[b * ldy + i] * w[i], v = g[b * ldg + i] * w[i];
         a_hi[e] = u;
         a_hi[plane + e] = v;
-        if (a_lo) {
-            a_lo[e] = tf32_lo(u);
-            a_lo[plane + e] = tf32_lo(v);
-        }
     }
 }
 
@@ -272,7 +253,7 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
     BackwardTables* T = p->bwd;
 
     const size_t plane = (size_t)batch * n;
-    const size_t bytes = sizeof(float) * 6 * plane + sizeof(double) * (2 * n + 2) + sizeof(float) * (2 * n + 8);
+    const size_t bytes = sizeof(float) * 4 * plane + sizeof(double) * (2 * n + 2) + sizeof(float) * (2 * n + 8);
     float* ws = static_cast<float*>(plan_workspace(p, st, bytes));
     if (!ws) return DCTPLUS_ERR_CUDA;
     const bool tc_shape = n % 128 == 0;
@@ -280,12 +261,8 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
 
     if (gx) {  // dLoss/dx = U (W^T g): transposed Cauchy product, then DCT-III
         float* t = ws;
-        float* g_lo = ws + plane;
-        if (tc_shape && aligned16(gy, ldg)) {
-            k_lo_rows<<<blocks_for(plane), 256, 0, st>>>(gy, ldg, n, batch, g_lo);
-            note_launch(st, "k_lo_rows", 8.0 * plane, 0.0);
-            DCTPLUS_CUDA_TRY(cudaGetLastError());
-            rc = launch_gemm_tc(gy, g_lo, ldg, T->wt_hi, T->wt_lo, n, t, n, (int)batch, n, n, st, cur);
+        if (tc_shape && aligned16(gy, ldg)) {  // g split on chip
+            rc = launch_gemm_tc(gy, nullptr, ldg, T->wt_hi, T->wt_lo, n, t, n, (int)batch, n, n, st, cur);
         } else {
             rc = launch_rows_gemm(gy, ldg, T->wt32, n, t, n, batch, n, n, st);
         }
@@ -297,19 +274,17 @@ extern "C" dctplus_status dctplus_backward(dctplus_plan_t p, const float* gy, in
     if (!want_params) return DCTPLUS_OK;
 
     float* a_hi = ws;               // 2 planes
-    float* a_lo = ws + 2 * plane;   // 2 planes
-    float* pq = ws + 4 * plane;     // 2 planes
-    double* rsum = reinterpret_cast<double*>(ws + 6 * plane);
+    float* pq = ws + 2 * plane;     // 2 planes
+    double* rsum = reinterpret_cast<double*>(ws + 4 * plane);
     double* t64 = rsum + n;
     double* grho = t64 + n;         // scratch when grad_rho is not wanted
     double* grho_out = grad_rho ? grad_rho : grho;
     const bool tc = tc_shape;
     DCTPLUS_CUDA_TRY(cudaMemsetAsync(rsum, 0, sizeof(double) * (n + n + 2), st));
-    k_param_prep<<<blocks_for(plane), 256, 0, st>>>(y, ldy, gy, ldg, T->w32, n, batch, a_hi,
-                                                    tc ? a_lo : nullptr);
-    note_launch(st, "k_param_prep", (tc ? 24.0 : 16.0) * plane, 2.0 * plane);
+    k_param_prep<<<blocks_for(plane), 256, 0, st>>>(y, ldy, gy, ldg, T->w32, n, batch, a_hi);
+    note_launch(st, "k_param_prep", 16.0 * plane, 2.0 * plane);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
-    rc = tc ? launch_gemm_tc(a_hi, a_lo, n, T->k_hi, T->k_lo, n, pq, n, (int)(2 * batch), n, n, st, cur)
+    rc = tc ? launch_gemm_tc(a_hi, nullptr, n, T->k_hi, T->k_lo, n, pq, n, (int)(2 * batch), n, n, st, cur)
             : launch_rows_gemm(a_hi, n, T->k32, n, pq, n, 2 * batch, n, n, st);
     if (rc != DCTPLUS_OK) return rc;
     dim3 grid((n + 255) / 256, (unsigned)((batch + kRedRows - 1) / kRedRows));

@@ -48,19 +48,26 @@ constexpr int kR = 12;  // Chebyshev degree of the far-field expansions
 struct HierTables {
     int nleaf = 0, Kw = 0;
     int nc = 0, ncp = 0;         // leaf coefficients nleaf R, padded to a multiple of 128
+    int ldl = 0;                 // row pitch of the leaf-local array: ncp + 32 (dense-row slots)
+    int Kx = 0;                  // far-field (L2P) columns per 128-row output tile, multiple of 32
     std::vector<int> kbeg;       // per 128-row output tile: first source of the K window
     float* slab_hi = nullptr;    // n x Kw
     float* slab_lo = nullptr;
     float* zf = nullptr;         // n: z_j (0 where deflated)
-    float* tq = nullptr;         // 64 x R: S_a at the 64 source positions of any leaf
-    float* pna = nullptr;        // n: -a_r for far-field targets, 0 otherwise
-    float* wl = nullptr;         // R x n: L2P weights -a_r S_a(u_r) (0 for other rows)
+    float* tq_hi = nullptr;      // 64 x kFarTqLd: S_a at the 64 source positions of any leaf
+    float* tq_lo = nullptr;
     int* row_leaf = nullptr;     // n
+    float* ext_hi = nullptr;     // n x (Kx + 32): L2P weights -a_r S_a(u_r) against the leaf-local
+    float* ext_lo = nullptr;     //   coefficients of the row's tile window, then the dense-row slots
     float* kf_hi = nullptr;      // ncp x ncp: leaf-to-leaf kernel samples, TF32 hi
     float* kf_lo = nullptr;      //            and lo (zero for near pairs and padding)
+    int* tab_l2l = nullptr;      // K-segment tables of the leaf-to-leaf and the output products
+    int* tab_out = nullptr;
+    int64_t chunks_l2l = 0, chunks_out = 0;
+    double acols_out = 0.0;
     int nout = 0;
     int out_row[2] = {-1, -1};
-    float* out_w = nullptr;      // nout x n dense rows
+    float* out_g = nullptr;      // nout x n: -a_o / (mu_o - lambda_j) of the dense rows
 };
 
 // round to TF32 (10 explicit mantissa bits), nearest-even; finite inputs
@@ -125,8 +132,8 @@ __global__ void k_band_slab(int n, int Kw, const int* kbeg_tile, const int* row_
 
 void free_hier(HierTables* h) {
     if (!h) return;
-    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf, h->tq, h->pna, h->wl, h->row_leaf,
-                    h->kf_hi, h->kf_lo, h->out_w};
+    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf,     h->tq_hi,   h->tq_lo,   h->row_leaf, h->ext_hi,
+                    h->ext_lo,  h->kf_hi,   h->kf_lo, h->tab_l2l, h->tab_out, h->out_g};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
@@ -171,9 +178,10 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         row_leaf[r] = std::min(std::max(lf, 0), nleaf - 1);
     }
 
-    // band windows per 128-row output tile
+    // band windows per 128-row output tile, and each tile's range of target leaves
     const int ntile = n / 128;
     h->kbeg.assign(ntile, 0);
+    std::vector<int> tile_lmin(ntile, 0), tile_lmax(ntile, -1);
     int kw = 0;
     for (int t = 0; t < ntile; ++t) {
         int lmin = nleaf, lmax = -1;
@@ -183,6 +191,8 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
             lmax = std::max(lmax, row_leaf[r]);
         }
         if (lmax < 0) { lmin = lmax = 0; }
+        tile_lmin[t] = lmin;
+        tile_lmax[t] = lmax;
         int k0 = (lmin - 1) * kLeaf, k1 = (lmax + 2) * kLeaf;
         h->kbeg[t] = k0;
         kw = std::max(kw, k1 - k0);
@@ -190,30 +200,96 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     h->Kw = (kw + 31) / 32 * 32;
 
     // P2M: every leaf holds 64 sources at the same relative positions, so the
-    // weights are z_j S_a(u_jj) with one 64 x R table; L2P: per-row position and -a_r
-    std::vector<float> zf(n), tq((size_t)kLeaf * kR), pna(n, 0.0f);
+    // weights are z_j S_a(u_jj) with one 64 x R table (split into TF32 hi / lo for
+    // the DCT kernel's tensor-core contraction); L2P: per-row position and -a_r
+    std::vector<float> zf(n), tq_hi((size_t)kLeaf * kFarTqLd, 0.0f), tq_lo((size_t)kLeaf * kFarTqLd, 0.0f);
     for (int j = 0; j < n; ++j) zf[j] = (float)znd[j];
     for (int jj = 0; jj < kLeaf; ++jj) {
         double u = (jj + 0.0) / kLeaf * 2.0 - 1.0;  // th_j within its leaf, scaled to [-1, 1)
-        for (int a = 0; a < kR; ++a) tq[(size_t)jj * kR + a] = (float)cheb_lagrange(a, u);
+        for (int a = 0; a < kR; ++a) {
+            const double v = cheb_lagrange(a, u);
+            const float hi = tf32_host((float)v);
+            tq_hi[(size_t)jj * kFarTqLd + a] = hi;
+            tq_lo[(size_t)jj * kFarTqLd + a] = tf32_host((float)(v - (double)hi));
+        }
     }
+    // leaf-local array per signal: nleaf R coefficients (leaf I at I R), padding to
+    // ncp, then 32 slots of which the first nout hold the dense rows' values
+    h->nc = nleaf * kR;
+    h->ncp = (h->nc + 127) / 128 * 128;
+    h->ldl = h->ncp + 32;
+    // L2P weights of each far-field target row against the leaf-local coefficients of
+    // its tile's window (leaves lmin .. lmax of the tile, starting at column lmin R)
+    int kx = 0;
+    for (int t = 0; t < ntile; ++t) kx = std::max(kx, (tile_lmax[t] - tile_lmin[t] + 1) * kR);
+    h->Kx = (kx + 31) / 32 * 32;
+    const int kxb = h->Kx + 32;
+    std::vector<float> ext_hi((size_t)n * kxb, 0.0f), ext_lo((size_t)n * kxb, 0.0f);
     for (int r = 0; r < n; ++r) {
-        if (row_leaf[r] < 0 || p->row_kind[r] == 0) continue;
-        pna[r] = (float)(-p->row_a[r]);
+        const int t = r / 128;
+        if (row_leaf[r] < 0) {  // dense row o: its value sits in slot o after the leaf window
+            for (int o = 0; o < h->nout; ++o)
+                if (h->out_row[o] == r) ext_hi[(size_t)r * kxb + h->Kx + o] = 1.0f;
+            continue;
+        }
+        if (p->row_kind[r] == 0) continue;  // deflated rows have no far field
+        const int b = row_leaf[r];
+        const double c = (b + 0.5) * hleaf, hw = 0.5 * hleaf;
+        for (int a = 0; a < kR; ++a) {
+            const double v = -p->row_a[r] * cheb_lagrange(a, (ph[r] - c) / hw);
+            const float hi = tf32_host((float)v);
+            const size_t at = (size_t)r * kxb + (size_t)(b - tile_lmin[t]) * kR + a;
+            ext_hi[at] = hi;
+            ext_lo[at] = tf32_host((float)(v - (double)hi));
+        }
     }
-    std::vector<float> wl((size_t)kR * n, 0.0f);
-    for (int r = 0; r < n; ++r) {
-        if (pna[r] == 0.0f) continue;
-        int b = row_leaf[r];
-        double c = (b + 0.5) * hleaf, hw = 0.5 * hleaf;
-        for (int a = 0; a < kR; ++a)
-            wl[(size_t)a * n + r] = (float)(-p->row_a[r] * cheb_lagrange(a, (ph[r] - c) / hw));
+    // segment tables (kGemmTabStride ints per 128-column output tile)
+    std::vector<int> tab_out((size_t)ntile * kGemmTabStride, 0);
+    h->chunks_out = 0;
+    h->acols_out = 0.0;
+    for (int t = 0; t < ntile; ++t) {
+        int* e = &tab_out[(size_t)t * kGemmTabStride];
+        int nseg = 0, nk = 0;
+        auto add = [&](int src, int acol, int bcol, int nch) {
+            e[2 + 4 * nseg] = src;
+            e[3 + 4 * nseg] = acol;
+            e[4 + 4 * nseg] = bcol;
+            e[5 + 4 * nseg] = nch;
+            ++nseg;
+            nk += nch;
+        };
+        // near field: the band of W against s, this tile's own width (the slab is zero
+        // beyond it)
+        add(0, h->kbeg[t], 0, (tile_lmax[t] - tile_lmin[t] + 3) * kLeaf / 32);
+        bool far = false, dense = false;
+        for (int r = 128 * t; r < 128 * t + 128; ++r) {
+            if (row_leaf[r] >= 0 && p->row_kind[r] == 1) far = true;
+            if (row_leaf[r] < 0) dense = true;
+        }
+        const int xw = (tile_lmax[t] - tile_lmin[t] + 1) * kR;
+        if (far) add(1, tile_lmin[t] * kR, 0, (xw + 31) / 32);  // far field: L2P of the leaf window
+        if (dense) add(1, h->ncp, h->Kx, 1);                    // dense rows: their values
+        e[0] = nseg;
+        e[1] = nk;
+        h->chunks_out += nk;
+        h->acols_out += (tile_lmax[t] - tile_lmin[t] + 3) * kLeaf + (far ? 32.0 * ((xw + 31) / 32) : 0.0) +
+                        (dense ? 32.0 : 0.0);
     }
+    h->acols_out = std::min(h->acols_out, (double)n + h->ldl);
+    std::vector<int> tab_l2l((size_t)(h->ncp / 128) * kGemmTabStride, 0);
+    for (int t = 0; t < h->ncp / 128; ++t) {
+        int* e = &tab_l2l[(size_t)t * kGemmTabStride];
+        e[0] = 1;
+        e[1] = (h->nc + 31) / 32;  // columns past nc of K_far are zero
+        e[2] = 0;
+        e[3] = 0;
+        e[4] = 0;
+        e[5] = (h->nc + 31) / 32;
+    }
+    h->chunks_l2l = (int64_t)(h->ncp / 128) * ((h->nc + 31) / 32);
     // leaf-to-leaf kernel 1 / (mu - lambda) = 1 / (2 cos th - 2 cos ph) at the
     // Chebyshev nodes of target leaf I (ph) and source leaf J (th), |I - J| >= 2;
     // rows (I, a), columns (J, b), zero-padded to ncp x ncp
-    h->nc = nleaf * kR;
-    h->ncp = (h->nc + 127) / 128 * 128;
     const int nc = h->nc, ncp = h->ncp;
     std::vector<float> kf_hi((size_t)ncp * ncp, 0.0f), kf_lo((size_t)ncp * ncp, 0.0f);
     {
@@ -235,13 +311,13 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
             }
         }
     }
-    // dense rows for eigenvalues outside [0, 4]
-    std::vector<float> outw((size_t)std::max(h->nout, 1) * n, 0.0f);
+    // dense rows for eigenvalues outside [0, 4]: W_oj = g_oj z_j with g_oj = -a_o / (mu_o - lambda_j)
+    std::vector<float> outg((size_t)std::max(h->nout, 1) * n, 0.0f);
     for (int o = 0; o < h->nout; ++o) {
         int r = h->out_row[o];
         for (int j = 0; j < n; ++j)
-            outw[(size_t)o * n + j] =
-                (float)w_entry(n, p->row_pole[r], p->row_tau[r], p->row_a[r], znd[j], j);
+            outg[(size_t)o * n + j] =
+                (float)w_entry(n, p->row_pole[r], p->row_tau[r], p->row_a[r], znd[j] != 0.0 ? 1.0 : 0.0, j);
     }
 
     auto up = [](auto** dst, const auto& v) -> cudaError_t {
@@ -250,13 +326,16 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         return cudaMemcpy(*dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice);
     };
     DCTPLUS_CUDA_TRY(up(&h->zf, zf));
-    DCTPLUS_CUDA_TRY(up(&h->tq, tq));
-    DCTPLUS_CUDA_TRY(up(&h->pna, pna));
-    DCTPLUS_CUDA_TRY(up(&h->wl, wl));
+    DCTPLUS_CUDA_TRY(up(&h->tq_hi, tq_hi));
+    DCTPLUS_CUDA_TRY(up(&h->tq_lo, tq_lo));
+    DCTPLUS_CUDA_TRY(up(&h->ext_hi, ext_hi));
+    DCTPLUS_CUDA_TRY(up(&h->ext_lo, ext_lo));
+    DCTPLUS_CUDA_TRY(up(&h->tab_out, tab_out));
+    DCTPLUS_CUDA_TRY(up(&h->tab_l2l, tab_l2l));
     DCTPLUS_CUDA_TRY(up(&h->row_leaf, row_leaf));
     DCTPLUS_CUDA_TRY(up(&h->kf_hi, kf_hi));
     DCTPLUS_CUDA_TRY(up(&h->kf_lo, kf_lo));
-    DCTPLUS_CUDA_TRY(up(&h->out_w, outw));
+    DCTPLUS_CUDA_TRY(up(&h->out_g, outg));
 
     int* d_kbeg = nullptr;
     DCTPLUS_CUDA_TRY(up(&d_kbeg, h->kbeg));
@@ -274,145 +353,21 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     return DCTPLUS_OK;
 }
 
-// ------------------------------------------------------------- far field
+// ------------------------------------------------------------- execute
 
-// the TF32 remainder of v for an operand whose hi part is v itself (the MMA
-// reads v truncated to TF32)
-__device__ __forceinline__ float lo_of(float v) {
-    return __uint_as_float(ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu)));
-}
-
-// P2M: mc[b][lf R + a] = sum over the 64 sources j of leaf lf of z_j S_a(u_j) s_bj
-// (and its TF32 remainder), and for each dense row o the partial dot product
-// po[b][2 lf + o] = sum over the same sources of out_w[o][j] s_bj. A warp takes
-// one leaf of 32 signals: it copies the 32 x 64 source block into shared
-// memory with coalesced loads (rows padded to 68 floats, so the per-signal
-// reads below are conflict-free), then each lane forms the values of its
-// signal; z, the S_a table and the dense rows are broadcast.
-constexpr int kP2mPitch = kLeaf + 4;
-__global__ void __launch_bounds__(256) k_p2m(int nleaf, const float* __restrict__ zf,
-                                             const float* __restrict__ tq, const float* __restrict__ s,
-                                             int64_t lds, int64_t batch, float* __restrict__ mc,
-                                             float* __restrict__ mc_lo, int ldm, int n, int nout,
-                                             const float* __restrict__ out_w, float* __restrict__ po) {
-    __shared__ __align__(16) float tqs[kLeaf * kR];
-    extern __shared__ __align__(16) float p2m_tile[];  // 8 warps x 32 x kP2mPitch
-    for (int e = threadIdx.x; e < kLeaf * kR; e += blockDim.x) tqs[e] = tq[e];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lf = blockIdx.y * 8 + warp;
-    if (lf >= nleaf) return;
-    const int64_t b0 = (int64_t)blockIdx.x * 32;
-    float* tile = p2m_tile + warp * 32 * kP2mPitch;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {  // all 16 loads in flight
-        const int row = 2 * k + (lane >> 4), c4 = lane & 15;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (b0 + row < batch)
-            v = *reinterpret_cast<const float4*>(s + (b0 + row) * lds + (int64_t)lf * kLeaf + 4 * c4);
-        *reinterpret_cast<float4*>(tile + row * kP2mPitch + 4 * c4) = v;
-    }
-    __syncwarp();
-    const float4* zp = reinterpret_cast<const float4*>(zf + (int64_t)lf * kLeaf);
-    const float* mine = tile + lane * kP2mPitch;
-    float acc[kR];
-#pragma unroll
-    for (int a = 0; a < kR; ++a) acc[a] = 0.f;
-    float od[2] = {0.f, 0.f};
-#pragma unroll 4
-    for (int j4 = 0; j4 < kLeaf / 4; ++j4) {
-        const float4 zv = __ldg(zp + j4);
-        const float4 sv = *reinterpret_cast<const float4*>(mine + 4 * j4);
-#pragma unroll
-        for (int o = 0; o < 2; ++o) {
-            if (o < nout) {
-                const float4 wv = __ldg(reinterpret_cast<const float4*>(out_w + (int64_t)o * n + (int64_t)lf * kLeaf) + j4);
-                od[o] = fmaf(wv.x, sv.x, fmaf(wv.y, sv.y, fmaf(wv.z, sv.z, fmaf(wv.w, sv.w, od[o]))));
-            }
-        }
-        const float w[4] = {sv.x * zv.x, sv.y * zv.y, sv.z * zv.z, sv.w * zv.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float4* t = reinterpret_cast<const float4*>(tqs + (4 * j4 + e) * kR);
-#pragma unroll
-            for (int q = 0; q < kR / 4; ++q) {
-                const float4 tv = t[q];
-                acc[4 * q + 0] = fmaf(w[e], tv.x, acc[4 * q + 0]);
-                acc[4 * q + 1] = fmaf(w[e], tv.y, acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(w[e], tv.z, acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(w[e], tv.w, acc[4 * q + 3]);
-            }
-        }
-    }
-    const int64_t b = b0 + lane;
-    if (b >= batch) return;
-    float4* out = reinterpret_cast<float4*>(mc + b * ldm + (int64_t)lf * kR);
-    float4* olo = reinterpret_cast<float4*>(mc_lo + b * ldm + (int64_t)lf * kR);
-#pragma unroll
-    for (int q = 0; q < kR / 4; ++q) {
-        out[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-        olo[q] = make_float4(lo_of(acc[4 * q]), lo_of(acc[4 * q + 1]), lo_of(acc[4 * q + 2]),
-                             lo_of(acc[4 * q + 3]));
-    }
-#pragma unroll
-    for (int o = 0; o < 2; ++o)
-        if (o < nout) po[b * 2 * nleaf + 2 * lf + o] = od[o];
-}
-
-// L2P: y[b][r] += sum_a wl[a][r] lc[b][leaf(r) R + a] for the far-field targets.
-// A thread keeps row r's weights in registers for 8 signals (block x: 8
-// signals, block y: 256 consecutive rows). The extra block row y = n / 256
-// writes the dense rows (eigenvalue outside [0, 4]): warp w sums, across its
-// lanes, the per-leaf partial dot products of signal 8 x + w.
-constexpr int kL2pSig = 8;
-__global__ void __launch_bounds__(256) k_l2p(int n, const float* __restrict__ wl,
-                                             const int* __restrict__ row_leaf,
-                                             const float* __restrict__ pna, const float* __restrict__ lc,
-                                             int ldm, float* __restrict__ y, int64_t ldy, int64_t batch,
-                                             int nleaf, int out_row0, int out_row1,
-                                             const float* __restrict__ po) {
-    const int64_t b0 = (int64_t)blockIdx.x * kL2pSig;
-    if ((int)blockIdx.y * 256 >= n) {
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int64_t b = b0 + w;
-        if (w >= kL2pSig || b >= batch) return;
-        for (int o = 0; o < 2; ++o) {
-            const int row = o == 0 ? out_row0 : out_row1;
-            if (row < 0) continue;
-            float t = 0.f;
-            for (int lf = lane; lf < nleaf; lf += 32) t += po[b * 2 * nleaf + 2 * lf + o];
-            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-            if (lane == 0) y[b * ldy + row] = t;
-        }
-        return;
-    }
-    const int r = blockIdx.y * 256 + threadIdx.x;
-    if (pna[r] == 0.f) return;
-    float w[kR];
-#pragma unroll
-    for (int a = 0; a < kR; ++a) w[a] = __ldg(wl + (int64_t)a * n + r);
-    const int leaf = row_leaf[r];
-#pragma unroll 4
-    for (int g = 0; g < kL2pSig; ++g) {
-        const int64_t b = b0 + g;
-        if (b >= batch) break;
-        const float4* l4 = reinterpret_cast<const float4*>(lc + b * ldm + (int64_t)leaf * kR);
-        float acc = 0.f;
-#pragma unroll
-        for (int q = 0; q < kR / 4; ++q) {
-            const float4 l = l4[q];
-            acc = fmaf(w[4 * q], l.x, fmaf(w[4 * q + 1], l.y, fmaf(w[4 * q + 2], l.z, fmaf(w[4 * q + 3], l.w, acc))));
-        }
-        y[b * ldy + r] += acc;
-    }
-}
-
-dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t lda, int Ka,
-                                   const float* b_hi, const float* b_lo, int64_t ldb, float* y,
-                                   int64_t ldy, int M, int N, int K, const int* kbeg,
-                                   cudaStream_t s, int dev);  // gemm_tc.cu
 void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes);
 
+// Three launches per batch:
+//   1. DCT-II (k_dct_far): s, the leaf moments (P2M) and the dense rows' values,
+//      which go to the dense-row slots of the leaf-local array (the slots after
+//      them are zeroed);
+//   2. leaf-to-leaf product (split-TF32 GEMM): leaf-local coefficients
+//      L = M K_far^T, into the leaf-local array;
+//   3. output product (split-TF32 GEMM over K segments): per 128-row tile the
+//      band of W against its window of s (near field), then the L2P weights
+//      against the tile's window of leaf-local coefficients (far field), then
+//      the dense rows' slots; y is written once.
+// The TF32 remainders of s, M and L are formed on chip by the GEMM.
 dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
                            int64_t batch, cudaStream_t st) {
     HierTables* h = p->hier;
@@ -420,44 +375,32 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     if (!h || batch > INT32_MAX || (reinterpret_cast<uintptr_t>(y) & 15) || (ldy & 3))
         return DCTPLUS_ERR_UNSUPPORTED;
     if (batch <= 0) return DCTPLUS_OK;
-    const size_t plane = (size_t)batch * n, cplane = (size_t)batch * h->ncp;
-    const size_t pplane = (size_t)batch * 2 * h->nleaf;
-    float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * (2 * plane + 3 * cplane + pplane)));
+    const size_t plane = (size_t)batch * n, cplane = (size_t)batch * h->ncp, lplane = (size_t)batch * h->ldl;
+    float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * (plane + cplane + lplane)));
     if (!ws) return DCTPLUS_ERR_CUDA;
     float* s_hi = ws;
-    float* s_lo = ws + plane;
-    float* mc = ws + 2 * plane;
-    float* mc_lo = mc + cplane;
-    float* lc = mc_lo + cplane;
-    float* po = lc + cplane;  // batch x 2 nleaf: the dense rows' per-leaf partial sums
-    dctplus_status r = launch_dct_fft(p, x, ldx, s_hi, s_lo, n, batch, st);
+    float* mc = ws + plane;
+    float* lc = mc + cplane;
+    DctFar far;
+    far.zf = h->zf;
+    far.tq_hi = h->tq_hi;
+    far.tq_lo = h->tq_lo;
+    far.mc = mc;
+    far.ldm = h->ncp;
+    far.out_g = h->out_g;
+    far.nout = h->nout;
+    far.dv = lc + h->ncp;
+    far.ldd = h->ldl;
+    dctplus_status r = launch_dct_far(p, x, ldx, s_hi, n, batch, far, st);
     if (r != DCTPLUS_OK) return r;
-    // far field first, while s is still in L2: leaf coefficients (and the dense
-    // rows' per-leaf partial sums), then the leaf-to-leaf product
-    const size_t p2m_smem = sizeof(float) * 8 * 32 * kP2mPitch;  // 69.6 KB
-    static bool p2m_attr[64] = {};
-    if (!p2m_attr[p->device & 63]) {
-        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem));
-        p2m_attr[p->device & 63] = true;
-    }
-    k_p2m<<<dim3((unsigned)((batch + 31) / 32), (unsigned)((h->nleaf + 7) / 8)), 256, p2m_smem, st>>>(
-        h->nleaf, h->zf, h->tq, s_hi, n, batch, mc, mc_lo, h->ncp, n, h->nout, h->out_w, po);
-    note_launch(st, "k_p2m", 4.0 * plane + 8.0 * cplane + 4.0 * pplane, 2.0 * kR * plane);
-    DCTPLUS_CUDA_TRY(cudaGetLastError());
-    r = launch_gemm_tc_band(mc, mc_lo, h->ncp, h->nc, h->kf_hi, h->kf_lo, h->ncp, lc, h->ncp,
-                            (int)batch, h->ncp, h->ncp, nullptr, st, p->device);
+    GemmSrc l2l{mc, nullptr, h->ncp, h->nc, h->kf_hi, h->kf_lo, h->ncp, h->ncp};
+    r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l, (double)h->nc, lc, nullptr, h->ldl,
+                            (int)batch, h->ncp, st, p->device, "k_gemm_tc");
     if (r != DCTPLUS_OK) return r;
-    // near field: y = band of W applied to s (dense rows get 0 here)
-    r = launch_gemm_tc_band(s_hi, s_lo, n, n, h->slab_hi, h->slab_lo, h->Kw, y, ldy, (int)batch, n,
-                            h->Kw, h->kbeg.data(), st, p->device);
-    if (r != DCTPLUS_OK) return r;
-    // far field added into y; the dense rows from their partial sums
-    k_l2p<<<dim3((unsigned)((batch + kL2pSig - 1) / kL2pSig), (unsigned)(n / 256 + (h->nout > 0))), 256, 0, st>>>(
-        n, h->wl, h->row_leaf, h->pna, lc, h->ncp, y, ldy, batch, h->nleaf,
-        h->nout > 0 ? h->out_row[0] : -1, h->nout > 1 ? h->out_row[1] : -1, po);
-    note_launch(st, "k_l2p", 8.0 * plane + 4.0 * cplane + 4.0 * pplane, 2.0 * kR * plane);
-    DCTPLUS_CUDA_TRY(cudaGetLastError());
-    return DCTPLUS_OK;
+    GemmSrc out[2] = {{s_hi, nullptr, n, n, h->slab_hi, h->slab_lo, h->Kw, h->Kw},
+                      {lc, nullptr, h->ldl, h->ldl, h->ext_hi, h->ext_lo, h->Kx + 32, h->Kx + 32}};
+    return launch_gemm_tc_segs(out, 2, h->tab_out, h->chunks_out, h->acols_out, y, nullptr, ldy,
+                               (int)batch, n, st, p->device, "k_gemm_tc");
 }
 
 }  // namespace dctplus

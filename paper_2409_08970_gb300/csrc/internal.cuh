@@ -148,6 +148,24 @@ void free_hier(HierTables* h);
 dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
                            int64_t batch, cudaStream_t st);
 
+// gemm_tc.cu: split-TF32 tensor-core product y = A B^T over K segments
+struct GemmSrc {
+    const float* a_hi;
+    const float* a_lo;
+    int64_t lda;
+    int Ka;              // A columns (TMA reads beyond read as zero)
+    const float* b_hi;
+    const float* b_lo;
+    int64_t ldb;
+    int Kb;              // B columns
+};
+constexpr int kGemmTabStride = 34;  // ints per column tile of a segment table
+constexpr int kGemmMaxSeg = 8;
+constexpr int kGemmBN = 128;         // output columns per tile
+dctplus_status launch_gemm_tc_segs(const GemmSrc* srcs, int nsrc, const int* tab, int64_t chunks_total,
+                                   double a_cols, float* y, float* y_lo, int64_t ldy, int M, int N,
+                                   cudaStream_t s, int dev, const char* name);
+
 // pruned.cu
 void pruned_forget(dctplus_plan_t p);  // drop cached stacked tables that use p
 // y[b][r] = sum_{k < Kd} a[b][k] w[r][k] for r < N on CUDA cores (any sizes)
@@ -166,17 +184,39 @@ dctplus_status launch_nfst(dctplus_plan_t p, const T* x, int64_t ldx, T* y, int6
 // small_simt.cu
 dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,
                                      int64_t ldy, int64_t batch, cudaStream_t s);
-dctplus_status launch_small_simt_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
-                                     int64_t ldy, int64_t batch, cudaStream_t s);
+
+// Far-field outputs of the DCT-II kernel for the hierarchical Cauchy product
+// (hier.cu): with s in shared memory the kernel also forms, per signal, the
+// leaf moments of the far field (P2M) and the values of the dense rows.
+constexpr int kFarR = 12;     // Chebyshev degree (moments per leaf)
+constexpr int kFarTqLd = 24;  // row pitch of the P2M table (conflict-free fragment loads)
+struct DctFar {
+    const float* zf;      // n: z_j, 0 where deflated
+    const float* tq_hi;   // 64 x kFarTqLd: S_a(u_jj) at the 64 source positions of a leaf
+    const float* tq_lo;   // (a < 12; other columns 0), TF32 hi and remainder
+    float* mc;            // leaf moments: mc[b * ldm + leaf * 12 + a] = sum_jj S_a(u_jj) z_j s_j
+    int64_t ldm;
+    const float* out_g;   // nout x n: for the rows whose eigenvalue mu_o lies outside [0, 4],
+    int nout;             // g_oj = -a_o / (mu_o - lambda_j) (0 where z_j = 0)
+    float* dv;            // their values dv[b * ldd + o] = sum_j g_oj z_j s_j (slots
+                          // nout .. 31 are written as zeros)
+    int64_t ldd;
+};
 
 // large.cu
+// DCT-II with the far-field outputs above (n a power of two in [256, 16384])
+dctplus_status launch_dct_far(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds,
+                              int64_t batch, const DctFar& far, cudaStream_t st);
 dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
-                              float* s_lo, int64_t lds, int64_t batch, cudaStream_t st);
-// DCT-III (inverse of the orthonormal DCT-II), n a power of two in [128, 8192]
+                              int64_t lds, int64_t batch, cudaStream_t st);
+// DCT-III (inverse of the orthonormal DCT-II), n a power of two in [128, 16384]
 dctplus_status launch_idct_fft(dctplus_plan_t p, const float* s, int64_t lds, float* x, int64_t ldx,
                                int64_t batch, cudaStream_t st);
 dctplus_status launch_cauchy_simt(dctplus_plan_t p, const float* s_in, int64_t lds, float* y,
                                   int64_t ldy, int64_t batch, cudaStream_t st);
+// FP64, n <= 64: a warp per signal
+dctplus_status launch_small_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
+                                int64_t ldy, int64_t batch, cudaStream_t st);
 dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
                                 int64_t ldy, int64_t batch, cudaStream_t st);
 dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, float* y,

@@ -2,9 +2,10 @@
 //
 // DCT-II (Algorithm 1 step 1) by Makhoul's reordering: v_k = x_2k,
 // v_{n-1-k} = x_{2k+1}; the length-n DFT of the real sequence v comes from one
-// complex FFT of length M = n/2 on w_m = v_2m + i v_2m+1 (radix-2 Stockham in
-// shared memory), and X_k = Re(exp(-i pi k / 2n) V_k), X_{n-k} = -Im(...).
-// The orthonormal scale c_k is folded into the last step.
+// complex FFT of length M = n/2 on w_m = v_2m + i v_2m+1 (in-place mixed-radix
+// passes in shared memory, radix 8 first), and X_k = Re(exp(-i pi k / 2n) V_k),
+// X_{n-k} = -Im(...). The orthonormal scale c_k is folded into the last step.
+// A variant also forms the hierarchical far field's leaf moments (k_dct_far).
 //
 // Cauchy product (Algorithm 1 steps 2-8 with a and z folded into
 // W_rk = -a_r z_k / (mu_r - lambda_k)): y = W s as a tiled CUDA-core GEMM. W
@@ -93,112 +94,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// TF32 remainder of v for the split-TF32 contractions: rn_tf32(v - trunc_tf32(v))
-__device__ __forceinline__ float tf32_lo(float v) {
-    return __uint_as_float(ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu)));
-}
-
-// One CTA per signal (grid-stride over the batch). The row is loaded with
-// coalesced (vector) loads into shared memory, reordered, and transformed by
-// a Stockham FFT of length M = n/2 with radix-4 stages (one radix-2 stage
-// first when log2 M is odd) and the twiddles staged in shared memory. With
-// s_lo non-null the TF32 remainder of every coefficient is written there too.
-__global__ void __launch_bounds__(512) k_dct_fft(int n, const float* __restrict__ x, int64_t ldx,
-                                                 float* __restrict__ s, float* __restrict__ s_lo,
-                                                 int64_t lds, int64_t batch,
-                                                 const float2* __restrict__ tw, int vec) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = n / 2;
-    float2* a = reinterpret_cast<float2*>(smem_raw);
-    float2* b = a + M;
-    float2* tws = b + M;  // M twiddles exp(-2 pi i j / M)
-    const float2* tw_split = tw + M;
-    const float2* tw_post = tw + 2 * M + 1;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int j = tid; j < M; j += nt) tws[j] = tw[j];
-    int log2M = 0;
-    while ((1 << log2M) < M) ++log2M;
-    for (int64_t sig = blockIdx.x; sig < batch; sig += gridDim.x) {
-        const float* xs = x + sig * ldx;
-        float* xf = reinterpret_cast<float*>(b);
-        __syncthreads();
-        if (vec) {
-            for (int i = tid; i < n / 4; i += nt)
-                reinterpret_cast<float4*>(xf)[i] = reinterpret_cast<const float4*>(xs)[i];
-        } else {
-            for (int i = tid; i < n; i += nt) xf[i] = xs[i];
-        }
-        __syncthreads();
-        // Makhoul reorder v_q = x_2q (q < M), x_{2n-2q-1} (q >= M); w_m = v_2m + i v_2m+1
-        for (int m = tid; m < M; m += nt) {
-            int q0 = 2 * m, q1 = 2 * m + 1;
-            float v0 = q0 < M ? xf[2 * q0] : xf[2 * n - 2 * q0 - 1];
-            float v1 = q1 < M ? xf[2 * q1] : xf[2 * n - 2 * q1 - 1];
-            a[m] = make_float2(v0, v1);
-        }
-        __syncthreads();
-        float2* src = a;
-        float2* dst = b;
-        int Ns = 1;
-        if (log2M & 1) {  // radix-2 stage with Ns = 1 (no twiddles)
-            for (int j = tid; j < M / 2; j += nt) {
-                float2 v0 = src[j], v1 = src[j + M / 2];
-                dst[2 * j] = make_float2(v0.x + v1.x, v0.y + v1.y);
-                dst[2 * j + 1] = make_float2(v0.x - v1.x, v0.y - v1.y);
-            }
-            __syncthreads();
-            float2* t = src; src = dst; dst = t;
-            Ns = 2;
-        }
-        for (; Ns < M; Ns <<= 2) {
-            const int tstep = M / (4 * Ns);
-            for (int j = tid; j < M / 4; j += nt) {
-                const int k = j & (Ns - 1);
-                float2 v0 = src[j], v1 = src[j + M / 4], v2 = src[j + M / 2], v3 = src[j + 3 * (M / 4)];
-                if (Ns > 1) {
-                    v1 = cmul(v1, tws[k * tstep]);
-                    v2 = cmul(v2, tws[2 * k * tstep]);
-                    v3 = cmul(v3, tws[3 * k * tstep]);
-                }
-                // 4-point DFT (exp(-2 pi i / 4) = -i)
-                float2 p0 = make_float2(v0.x + v2.x, v0.y + v2.y), p1 = make_float2(v0.x - v2.x, v0.y - v2.y);
-                float2 q0 = make_float2(v1.x + v3.x, v1.y + v3.y), q1 = make_float2(v1.x - v3.x, v1.y - v3.y);
-                const int o = ((j - k) << 2) + k;
-                dst[o] = make_float2(p0.x + q0.x, p0.y + q0.y);
-                dst[o + Ns] = make_float2(p1.x + q1.y, p1.y - q1.x);
-                dst[o + 2 * Ns] = make_float2(p0.x - q0.x, p0.y - q0.y);
-                dst[o + 3 * Ns] = make_float2(p1.x - q1.y, p1.y + q1.x);
-            }
-            __syncthreads();
-            float2* t = src; src = dst; dst = t;
-        }
-        float* ss = s + sig * lds;
-        for (int k = threadIdx.x; k <= M; k += blockDim.x) {
-            float2 wk = src[k == M ? 0 : k];
-            float2 wm = src[(M - k) == M ? 0 : (M - k)];
-            float2 wmc = make_float2(wm.x, -wm.y);
-            float2 fe = make_float2(0.5f * (wk.x + wmc.x), 0.5f * (wk.y + wmc.y));
-            float2 d = make_float2(wk.x - wmc.x, wk.y - wmc.y);
-            float2 fo = make_float2(0.5f * d.y, -0.5f * d.x);  // d / (2i)
-            float2 vk = make_float2(fe.x, fe.y);
-            float2 t = cmul(tw_split[k], fo);
-            vk.x += t.x; vk.y += t.y;
-            float2 bq = cmul(tw_post[k], vk);  // c_k exp(-i pi k/2n) V_k
-            if (k == 0 || k == M) {
-                ss[k] = bq.x;
-                if (s_lo) s_lo[sig * lds + k] = tf32_lo(bq.x);
-            } else {
-                ss[k] = bq.x;
-                // X_{n-k} = -Im(exp(-i pi k/2n) V_k); c_{n-k} = c_k for k > 0
-                ss[n - k] = -bq.y;
-                if (s_lo) {
-                    s_lo[sig * lds + k] = tf32_lo(bq.x);
-                    s_lo[sig * lds + n - k] = tf32_lo(-bq.y);
-                }
-            }
-        }
-    }
-}
 
 __host__ __device__ constexpr int bit_reverse(int i, int bits) {
     int r = 0;
@@ -245,13 +140,17 @@ __host__ __device__ constexpr int fft_tw_offset(int M, int B) {
     return off;
 }
 
+// Threads per signal of the radix-8 FFT kernels: one per radix-8 butterfly
+// (M / 8), at most 512 (then each thread takes several butterflies per pass).
+__host__ __device__ constexpr int fft_tps(int M) { return M / 8 < 512 ? M / 8 : 512; }
+
 // One in-place decimation-in-frequency pass on blocks of B points, radix R:
 // butterfly (b, n1) takes the R points b B + n1 + r S (S = B / R), a length-R
 // DFT in registers, twiddles exp(-2 pi i n1 k2 / B), and puts output k2 back at
 // b B + n1 + k2 S. Each thread writes exactly the points it read.
 template <int M, int B>
 __device__ __forceinline__ void fft_pass(float2* buf, int t, const float2* __restrict__ twp) {
-    constexpr int R = fft_radix(B), S = B / R, TPS = M / 8, PER = (M / R) / TPS;
+    constexpr int R = fft_radix(B), S = B / R, TPS = fft_tps(M), PER = (M / R) / TPS;
     const float2* tw = twp + fft_tw_offset(M, B);
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
@@ -286,17 +185,54 @@ __device__ __forceinline__ int fft_out_pos(int k) {
     return pos;
 }
 
+// Makhoul-ordered load of one signal into its FFT buffer:
+// w_q = x_4q + i x_4q+2, w_{M-1-q} = x_4q+3 + i x_4q+1
+template <int M>
+__device__ __forceinline__ void dct_load(float2* buf, const float* xs, int t, int vec) {
+    constexpr int TPS = fft_tps(M);
+    constexpr int kLoads = M / 2 / TPS;
+    float4 v[kLoads];
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) {
+        const int q = t + i * TPS;
+        if (vec) v[i] = __ldg(reinterpret_cast<const float4*>(xs) + q);
+        else v[i] = make_float4(xs[4 * q], xs[4 * q + 1], xs[4 * q + 2], xs[4 * q + 3]);
+    }
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) {
+        const int q = t + i * TPS;
+        buf[fft_phys(q)] = make_float2(v[i].x, v[i].z);
+        buf[fft_phys(M - 1 - q)] = make_float2(v[i].w, v[i].y);
+    }
+}
+
+// Split and post-twiddle for the output pair (k, M - k), 0 <= k <= M / 2:
+// s_k = bk.x, s_{n-k} = -bk.y (k > 0), s_{M-k} = bp.x, s_{n-M+k} = -bp.y
+// (the last two only for M - k != k, and s_{n-M+k} only for k > 0).
+template <int M>
+__device__ __forceinline__ void dct_post(const float2* buf, int k, const float2* __restrict__ tw_split,
+                                         const float2* __restrict__ tw_post, float2& bk, float2& bp) {
+    const float2 xk = buf[fft_phys(fft_out_pos<M>(k))];
+    const float2 xm = buf[fft_phys(fft_out_pos<M>((M - k) & (M - 1)))];
+    const float2 fe = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
+    const float2 fo = make_float2(0.5f * (xk.y + xm.y), -0.5f * (xk.x - xm.x));  // (xk - conj xm) / 2i
+    float2 tt = cmul(__ldg(tw_split + k), fo);
+    bk = cmul(__ldg(tw_post + k), make_float2(fe.x + tt.x, fe.y + tt.y));
+    const int kp = M - k;
+    tt = cmul(__ldg(tw_split + kp), make_float2(fo.x, -fo.y));
+    bp = cmul(__ldg(tw_post + kp), make_float2(fe.x + tt.x, -fe.y + tt.y));
+}
+
 // DCT-II by Makhoul's reordering and an in-place mixed-radix FFT of length
-// M = n / 2 in shared memory (radix-8 passes, M / 8 threads per signal, each
-// butterfly's points in registers), then the split and post-twiddle. Several
-// signals per CTA. Loads are float4 (when aligned) and the stores of s (and its
-// TF32 remainder s_lo) are four coalesced streams.
+// M = n / 2 in shared memory (radix-8 passes, fft_tps(M) threads per signal,
+// each butterfly's points in registers), then the split and post-twiddle.
+// Several signals per CTA. Loads are float4 (when aligned) and the stores of s
+// are four coalesced streams.
 template <int M>
 __global__ void __launch_bounds__(512) k_dct_r8(int n, const float* __restrict__ x, int64_t ldx,
-                                                float* __restrict__ s, float* __restrict__ s_lo,
-                                                int64_t lds, int64_t batch,
+                                                float* __restrict__ s, int64_t lds, int64_t batch,
                                                 const float2* __restrict__ tw, int vec) {
-    constexpr int TPS = M / 8;
+    constexpr int TPS = fft_tps(M);
     constexpr int BUF = M + M / 8;  // float2 per signal
     extern __shared__ __align__(16) float2 dsm[];
     const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
@@ -309,65 +245,35 @@ __global__ void __launch_bounds__(512) k_dct_r8(int n, const float* __restrict__
         const int64_t sig = base + slot;
         const bool live = sig < batch;
         __syncthreads();
-        if (live) {  // w_q = x_4q + i x_4q+2, w_{M-1-q} = x_4q+3 + i x_4q+1 (Makhoul order)
-            const float* xs = x + sig * ldx;
-            constexpr int kLoads = M / 2 / TPS;
-            float4 v[kLoads];
-#pragma unroll
-            for (int i = 0; i < kLoads; ++i) {
-                const int q = t + i * TPS;
-                if (vec) v[i] = __ldg(reinterpret_cast<const float4*>(xs) + q);
-                else v[i] = make_float4(xs[4 * q], xs[4 * q + 1], xs[4 * q + 2], xs[4 * q + 3]);
-            }
-#pragma unroll
-            for (int i = 0; i < kLoads; ++i) {
-                const int q = t + i * TPS;
-                buf[fft_phys(q)] = make_float2(v[i].x, v[i].z);
-                buf[fft_phys(M - 1 - q)] = make_float2(v[i].w, v[i].y);
-            }
-        }
+        if (live) dct_load<M>(buf, x + sig * ldx, t, vec);
         __syncthreads();
         fft_pass<M, M>(buf, t, twp);
         if (!live) continue;
         float* ss = s + sig * lds;
-        float* sl = s_lo ? s_lo + sig * lds : nullptr;
         constexpr int kPost = (M / 2 + TPS) / TPS;  // covers k = 0 .. M / 2
 #pragma unroll
         for (int i = 0; i < kPost; ++i) {
             const int k = t + i * TPS;
             if (k > M / 2) break;
-            const float2 xk = buf[fft_phys(fft_out_pos<M>(k))];
-            const float2 xm = buf[fft_phys(fft_out_pos<M>((M - k) & (M - 1)))];
-            const float2 fe = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
-            const float2 fo = make_float2(0.5f * (xk.y + xm.y), -0.5f * (xk.x - xm.x));  // (xk - conj xm) / 2i
-            float2 tt = cmul(__ldg(tw_split + k), fo);
-            const float2 bk = cmul(__ldg(tw_post + k), make_float2(fe.x + tt.x, fe.y + tt.y));
+            float2 bk, bp;
+            dct_post<M>(buf, k, tw_split, tw_post, bk, bp);
             ss[k] = bk.x;
-            if (sl) sl[k] = tf32_lo(bk.x);
-            if (k > 0) {
-                ss[n - k] = -bk.y;
-                if (sl) sl[n - k] = tf32_lo(-bk.y);
-            }
+            if (k > 0) ss[n - k] = -bk.y;
             const int kp = M - k;
             if (kp != k) {
-                tt = cmul(__ldg(tw_split + kp), make_float2(fo.x, -fo.y));
-                const float2 bp = cmul(__ldg(tw_post + kp), make_float2(fe.x + tt.x, -fe.y + tt.y));
                 ss[kp] = bp.x;
-                if (sl) sl[kp] = tf32_lo(bp.x);
-                if (kp != M) {
-                    ss[n - kp] = -bp.y;
-                    if (sl) sl[n - kp] = tf32_lo(-bp.y);
-                }
+                if (kp != M) ss[n - kp] = -bp.y;
             }
         }
     }
 }
 
-// CTA shape for the radix-8 kernels: M / 8 threads per signal, up to 256 threads,
+// CTA shape for the radix-8 kernels: fft_tps(M) threads per signal, up to 256 threads
+// (512 when one signal needs them),
 // but small batches spread over all SMs
 template <int M>
 static void r8_shape(int64_t batch, int dev, int* spc_out, size_t* smem_out, int64_t* grid_out) {
-    constexpr int TPS = M / 8;
+    constexpr int TPS = fft_tps(M);
     constexpr size_t kBufBytes = sizeof(float2) * (M + M / 8);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -384,8 +290,7 @@ static void r8_shape(int64_t batch, int dev, int* spc_out, size_t* smem_out, int
 }
 
 template <int M>
-static dctplus_status launch_r8(int n, const float* x, int64_t ldx, float* s_out, float* s_lo,
-                                int64_t lds, int64_t batch, const float2* tw, int vec,
+static dctplus_status launch_r8(int n, const float* x, int64_t ldx, float* s_out, int64_t lds, int64_t batch, const float2* tw, int vec,
                                 cudaStream_t st, int dev) {
     int spc;
     size_t smem;
@@ -399,10 +304,228 @@ static dctplus_status launch_r8(int n, const float* x, int64_t ldx, float* s_out
             attr[dev & 63] = true;
         }
     }
-    k_dct_r8<M><<<(unsigned)grid, spc * (M / 8), smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec);
-    note_launch(st, "k_dct_r8", (s_lo ? 12.0 : 8.0) * batch * n, dct_flops(n) * batch);
+    k_dct_r8<M><<<(unsigned)grid, spc * fft_tps(M), smem, st>>>(n, x, ldx, s_out, lds, batch, tw, vec);
+    note_launch(st, "k_dct_r8", 8.0 * batch * n, dct_flops(n) * batch);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
+}
+
+// ------------------------------------------------- DCT-II + far-field moments
+
+// D += A B for one m16n8k8 TF32 tile (mma.sync). The leaf-moment contraction
+// below is a few multiply-adds per sample inside a CUDA-core kernel, too small
+// to pay for a tcgen05 pipeline; the warp-level instruction keeps it off the
+// FMA pipe that the FFT saturates.
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], const uint32_t (&a)[4],
+                                                 const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// shared-memory index of coefficient j in the P2M staging buffer: 4 pad
+// floats per leaf of 64 keep the fragment loads conflict-free
+__device__ __forceinline__ int far_phys(int j) { return j + 4 * (j >> 6); }
+
+// DCT-II (as k_dct_r8) plus the hierarchical far field's per-signal inputs:
+//   leaf moments  mc[b][leaf 12 + a] = sum_{jj < 64} S_a(u_jj) z_j s_j, j = 64 leaf + jj
+//                 (P2M: z-weighted Chebyshev interpolation coefficients of the
+//                 leaf's sources), with their TF32 remainders;
+//   dense rows    dv[b][o] = sum_j W_oj s_j = sum_j g_oj w_j for the rows whose
+//                 eigenvalue lies outside [0, 4] (no angle, so no leaf), with
+//                 g_oj = -a_o / (mu_o - lambda_j) and w_j = z_j s_j.
+// The post-twiddle also writes w_j = z_j s_j into a separate shared buffer
+// (padded by far_phys); the moments are one [rows = (signal, leaf)] x [K = 64] x [N = 12] contraction
+// per CTA on the tensor cores in split TF32 (A_hi B_lo + A_lo B_hi + A_hi B_hi,
+// each k-step accumulated fresh and added in FP32): one m16n8k8 row tile of 16
+// (signal, leaf) rows per warp. The dense rows are read off the same w buffer
+// and reduce over the signal's threads.
+template <int M>
+__global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restrict__ x, int64_t ldx,
+                                                 float* __restrict__ s, int64_t lds, int64_t batch,
+                                                 const float2* __restrict__ tw, int vec, const DctFar F) {
+    constexpr int TPS = fft_tps(M);
+    constexpr int BUF = M + M / 8;
+    constexpr int WB = 2 * M + M / 8;  // floats of a signal's w buffer (far_phys(n - 1) < WB)
+    constexpr int NLEAF = M / 32;      // n / 64
+    constexpr int kPost = (M / 2 + TPS) / TPS;
+    constexpr int kWps = (TPS + 31) / 32;  // warps (or the part of one) per signal
+    extern __shared__ __align__(16) float2 dsm[];
+    const int spc = blockDim.x / TPS;
+    const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2* buf = dsm + slot * BUF;
+    float* wall = reinterpret_cast<float*>(dsm + spc * BUF);  // [spc][WB]: w = z s
+    float* wb = wall + slot * WB;
+    float* tqs = wall + spc * WB;                              // [2][64][kFarTqLd]: hi, lo
+    float* red = tqs + 2 * 64 * kFarTqLd;                      // [spc][kWps][2]
+    const float2* __restrict__ tw_split = tw + M;
+    const float2* __restrict__ tw_post = tw + 2 * M + 1;
+    const float2* __restrict__ twp = tw + 3 * M + 2;
+    for (int e = threadIdx.x; e < 64 * kFarTqLd; e += blockDim.x) {
+        tqs[e] = F.tq_hi[e];
+        tqs[64 * kFarTqLd + e] = F.tq_lo[e];
+    }
+    const int ntile = (spc * NLEAF + 15) / 16;  // P2M row tiles of this CTA
+    for (int64_t base = (int64_t)blockIdx.x * spc; base < batch; base += (int64_t)gridDim.x * spc) {
+        const int64_t sig = base + slot;
+        const bool live = sig < batch;
+        __syncthreads();  // the previous iteration's P2M has read the w buffers
+        if (live) dct_load<M>(buf, x + sig * ldx, t, vec);
+        __syncthreads();
+        fft_pass<M, M>(buf, t, twp);
+        float d0 = 0.f, d1 = 0.f;  // dense-row partial sums
+        if (live) {
+            float* ss = s + sig * lds;
+#pragma unroll
+            for (int i = 0; i < kPost; ++i) {
+                const int k = t + i * TPS;
+                if (k > M / 2) break;
+                float2 bk, bp;
+                dct_post<M>(buf, k, tw_split, tw_post, bk, bp);
+                const int kp = M - k;
+                const float val[4] = {bk.x, -bk.y, bp.x, -bp.y};
+                const int pos[4] = {k, n - k, kp, n - kp};
+                const bool use[4] = {true, k > 0, kp != k, kp != k && kp != M};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (!use[e]) continue;
+                    ss[pos[e]] = val[e];
+                    wb[far_phys(pos[e])] = __ldg(F.zf + pos[e]) * val[e];
+                }
+            }
+        }
+        __syncthreads();
+        if (F.nout > 0) {  // dense rows: sum_j g_oj w_j over the signal's threads
+            if (live) {
+                for (int j = t; j < n; j += TPS) {
+                    const float wj = wb[far_phys(j)];
+                    d0 = fmaf(__ldg(F.out_g + j), wj, d0);
+                    if (F.nout > 1) d1 = fmaf(__ldg(F.out_g + n + j), wj, d1);
+                }
+            }
+            constexpr int width = TPS < 32 ? TPS : 32;
+#pragma unroll
+            for (int off = width / 2; off > 0; off >>= 1) {
+                d0 += __shfl_xor_sync(0xffffffffu, d0, off);
+                d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+            }
+            if ((t & (width - 1)) == 0) {
+                red[(slot * kWps + t / 32) * 2 + 0] = d0;
+                red[(slot * kWps + t / 32) * 2 + 1] = d1;
+            }
+        }
+        if (warp < ntile) {  // P2M: rows (signal slot, leaf) 16 w .. 16 w + 15
+            const int g = lane >> 2, tg = lane & 3;
+            const float* wrow[2];
+            int64_t rsig[2];
+            int rleaf[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = 16 * warp + g + 8 * h;
+                const int sl_ = r / NLEAF;
+                rleaf[h] = r % NLEAF;
+                rsig[h] = base + sl_;
+                const bool ok = sl_ < spc && rsig[h] < batch;
+                wrow[h] = ok ? wall + sl_ * WB + rleaf[h] * 68 : nullptr;
+                if (!ok) rsig[h] = -1;
+            }
+            float acc[2][4] = {};
+#pragma unroll 1
+            for (int ks = 0; ks < 8; ++ks) {
+                const int k0 = 8 * ks + tg;
+                const float af[4] = {wrow[0] ? wrow[0][k0] : 0.f, wrow[1] ? wrow[1][k0] : 0.f,
+                                     wrow[0] ? wrow[0][k0 + 4] : 0.f, wrow[1] ? wrow[1][k0 + 4] : 0.f};
+                uint32_t ahi[4], alo[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    ahi[e] = __float_as_uint(af[e]) & ~0x1FFFu;
+                    alo[e] = ptx::cvt_rna_tf32(af[e] - __uint_as_float(ahi[e]));
+                }
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const int c = 8 * nt + g;
+                    const uint32_t bhi[2] = {__float_as_uint(tqs[k0 * kFarTqLd + c]),
+                                             __float_as_uint(tqs[(k0 + 4) * kFarTqLd + c])};
+                    const uint32_t blo[2] = {__float_as_uint(tqs[64 * kFarTqLd + k0 * kFarTqLd + c]),
+                                             __float_as_uint(tqs[64 * kFarTqLd + (k0 + 4) * kFarTqLd + c])};
+                    float d[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_m16n8k8_tf32(d, ahi, blo);
+                    mma_m16n8k8_tf32(d, alo, bhi);
+                    mma_m16n8k8_tf32(d, ahi, bhi);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[nt][e] += d[e];
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int h = e >> 1, a = 8 * nt + 2 * tg + (e & 1);
+                    if (a >= kFarR || rsig[h] < 0) continue;
+                    const int64_t o = rsig[h] * F.ldm + rleaf[h] * kFarR + a;
+                    F.mc[o] = acc[nt][e];
+                }
+        }
+        __syncthreads();  // the dense rows' partial sums are in red
+        if (live) {  // the 32 dense-row slots: values, then zeros
+            for (int o = t; o < 32; o += TPS) {
+                float val = 0.f;
+                if (o < F.nout)
+                    for (int w = 0; w < kWps; ++w) val += red[(slot * kWps + w) * 2 + o];
+                F.dv[sig * F.ldd + o] = val;
+            }
+        }
+    }
+}
+
+template <int M>
+static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_out, int64_t lds, int64_t batch, const float2* tw, int vec,
+                                 const DctFar& F, cudaStream_t st, int dev) {
+    constexpr int TPS = fft_tps(M);
+    constexpr int kWps = (TPS + 31) / 32;
+    int spc;
+    size_t smem;
+    int64_t grid;
+    r8_shape<M>(batch, dev, &spc, &smem, &grid);
+    if (spc * TPS < 32) {  // whole warps for the moment contraction and the reductions
+        spc = 32 / TPS;
+        grid = std::min<int64_t>(grid, (batch + spc - 1) / spc);
+    }
+    smem = (size_t)spc * sizeof(float2) * (M + M / 8) +
+           sizeof(float) * ((size_t)spc * (2 * M + M / 8) + 2 * 64 * kFarTqLd + spc * kWps * 2);
+    static bool attr[64] = {};
+    if (!attr[dev & 63]) {
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_far<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              200 * 1024));
+        attr[dev & 63] = true;
+    }
+    k_dct_far<M><<<(unsigned)grid, spc * TPS, smem, st>>>(n, x, ldx, s_out, lds, batch, tw, vec, F);
+    note_launch(st, "k_dct_far",
+                8.0 * batch * n + 4.0 * batch * (n / 64) * kFarR + 4.0 * 32 * batch,
+                dct_flops(n) * batch + 6.0 * kFarR * (double)batch * n + 2.0 * F.nout * (double)batch * n);
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+dctplus_status launch_dct_far(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds, int64_t batch, const DctFar& far, cudaStream_t st) {
+    const int n = p->n;
+    if (!p->d_twiddle || batch > INT32_MAX || far.nout > 2) return DCTPLUS_ERR_UNSUPPORTED;
+    if (batch <= 0) return DCTPLUS_OK;
+    const int vec = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
+    const float2* tw = reinterpret_cast<const float2*>(p->d_twiddle);
+    switch (n) {
+        case 256: return launch_far<128>(n, x, ldx, s_out, lds, batch, tw, vec, far, st, p->device);
+        case 512: return launch_far<256>(n, x, ldx, s_out, lds, batch, tw, vec, far, st, p->device);
+        case 1024: return launch_far<512>(n, x, ldx, s_out, lds, batch, tw, vec, far, st, p->device);
+        case 2048: return launch_far<1024>(n, x, ldx, s_out, lds, batch, tw, vec, far, st, p->device);
+        case 4096: return launch_far<2048>(n, x, ldx, s_out, lds, batch, tw, vec, far, st, p->device);
+        case 8192: return launch_far<4096>(n, x, ldx, s_out, lds, batch, tw, vec, far, st, p->device);
+        case 16384: return launch_far<8192>(n, x, ldx, s_out, lds, batch, tw, vec, far, st, p->device);
+        default: return DCTPLUS_ERR_UNSUPPORTED;
+    }
 }
 
 // Inverse of k_dct_r8 (DCT-III, x = U s, orthonormal): undo the post-twiddle
@@ -416,7 +539,7 @@ template <int M>
 __global__ void __launch_bounds__(512) k_idct_r8(int n, const float* __restrict__ s, int64_t lds,
                                                  float* __restrict__ x, int64_t ldx, int64_t batch,
                                                  const float2* __restrict__ tw, int vec) {
-    constexpr int TPS = M / 8;
+    constexpr int TPS = fft_tps(M);
     constexpr int BUF = M + M / 8;
     extern __shared__ __align__(16) float2 dsm[];
     const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
@@ -498,7 +621,7 @@ static dctplus_status launch_ir8(int n, const float* s, int64_t lds, float* x, i
             attr[dev & 63] = true;
         }
     }
-    k_idct_r8<M><<<(unsigned)grid, spc * (M / 8), smem, st>>>(n, s, lds, x, ldx, batch, tw, vec);
+    k_idct_r8<M><<<(unsigned)grid, spc * fft_tps(M), smem, st>>>(n, s, lds, x, ldx, batch, tw, vec);
     note_launch(st, "k_idct_r8", 8.0 * batch * n, dct_flops(n) * batch);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
@@ -519,12 +642,13 @@ dctplus_status launch_idct_fft(dctplus_plan_t p, const float* s, int64_t lds, fl
         case 2048: return launch_ir8<1024>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
         case 4096: return launch_ir8<2048>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
         case 8192: return launch_ir8<4096>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
+        case 16384: return launch_ir8<8192>(n, s, lds, x, ldx, batch, tw, vec4, st, p->device);
         default: return DCTPLUS_ERR_UNSUPPORTED;
     }
 }
 
 dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
-                              float* s_lo, int64_t lds, int64_t batch, cudaStream_t st) {
+                              int64_t lds, int64_t batch, cudaStream_t st) {
     int n = p->n;
     if (!p->d_twiddle) return DCTPLUS_ERR_UNSUPPORTED;
     if (batch <= 0) return DCTPLUS_OK;
@@ -532,33 +656,18 @@ dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, flo
         const int vec4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
         const float2* tw = reinterpret_cast<const float2*>(p->d_twiddle);
         switch (n) {
-            case 128: return launch_r8<64>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 256: return launch_r8<128>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 512: return launch_r8<256>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 1024: return launch_r8<512>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 2048: return launch_r8<1024>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 4096: return launch_r8<2048>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
-            case 8192: return launch_r8<4096>(n, x, ldx, s_out, s_lo, lds, batch, tw, vec4, st, p->device);
+            case 128: return launch_r8<64>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
+            case 256: return launch_r8<128>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
+            case 512: return launch_r8<256>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
+            case 1024: return launch_r8<512>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
+            case 2048: return launch_r8<1024>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
+            case 4096: return launch_r8<2048>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
+            case 8192: return launch_r8<4096>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
+            case 16384: return launch_r8<8192>(n, x, ldx, s_out, lds, batch, tw, vec4, st, p->device);
             default: break;
         }
     }
-    size_t smem = sizeof(float2) * 3 * (n / 2);  // two ping-pong buffers + twiddles
-    static bool attr[64] = {};
-    if (!attr[p->device & 63]) {
-        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-        attr[p->device & 63] = true;
-    }
-    int threads = std::min(512, std::max(32, n / 8));
-    int per_sm = std::max(1, std::min((int)(220 * 1024 / smem), 2048 / threads));
-    int64_t grid = std::min<int64_t>(batch, (int64_t)152 * per_sm * 2);
-    if (grid <= 0) return DCTPLUS_OK;
-    const int vec = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
-    k_dct_fft<<<(unsigned)grid, threads, smem, st>>>(n, x, ldx, s_out, s_lo, lds, batch,
-                                                     reinterpret_cast<const float2*>(p->d_twiddle),
-                                                     vec);
-    note_launch(st, "k_dct_fft", (s_lo ? 12.0 : 8.0) * batch * n, dct_flops(n) * batch);
-    DCTPLUS_CUDA_TRY(cudaGetLastError());
-    return DCTPLUS_OK;
+    return DCTPLUS_ERR_UNSUPPORTED;
 }
 
 // ------------------------------------------------------- Cauchy (CUDA cores)
@@ -697,6 +806,70 @@ __global__ void __launch_bounds__(256) k_dense_f64(int n, const double* __restri
     }
 }
 
+// FP64 for n <= 64: a warp per signal, lane l owns output coefficients l and l + 32;
+// U^T and W are staged transposed in shared memory once per CTA, so that the
+// lanes read consecutive entries, and each x_j (then s_j) is broadcast by a shuffle.
+constexpr int kF64SmallWarps = 8;
+__global__ void __launch_bounds__(32 * kF64SmallWarps) k_small_f64(int n, const double* __restrict__ x,
+                                                                   int64_t ldx, double* __restrict__ y,
+                                                                   int64_t ldy, int64_t batch,
+                                                                   const double* __restrict__ ct,
+                                                                   const double* __restrict__ w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* cts = reinterpret_cast<double*>(smem_raw);  // [j][k] = U^T[k][j]
+    double* wts = cts + n * n;                          // [j][k] = W[k][j]
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int k = e / n, j = e % n;
+        cts[j * n + k] = ct[e];
+        wts[j * n + k] = w[e];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool has0 = lane < n, has1 = lane + 32 < n;
+    for (int64_t b = (int64_t)blockIdx.x * kF64SmallWarps + warp; b < batch;
+         b += (int64_t)gridDim.x * kF64SmallWarps) {
+        const double* xs = x + b * ldx;
+        const double x0 = has0 ? xs[lane] : 0.0, x1 = has1 ? xs[lane + 32] : 0.0;
+        double s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+            if (has0) s0 = fma(cts[j * n + lane], xj, s0);
+            if (has1) s1 = fma(cts[j * n + lane + 32], xj, s1);
+        }
+        double y0 = 0.0, y1 = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double sj = __shfl_sync(0xffffffffu, j < 32 ? s0 : s1, j & 31);
+            if (has0) y0 = fma(wts[j * n + lane], sj, y0);
+            if (has1) y1 = fma(wts[j * n + lane + 32], sj, y1);
+        }
+        double* ys = y + b * ldy;
+        if (has0) ys[lane] = y0;
+        if (has1) ys[lane + 32] = y1;
+    }
+}
+
+dctplus_status launch_small_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
+                                int64_t ldy, int64_t batch, cudaStream_t st) {
+    const int n = p->n;
+    if (!p->d_ct64 || !p->d_w64 || n > kSmallMax) return DCTPLUS_ERR_UNSUPPORTED;
+    const size_t smem = sizeof(double) * 2 * n * n;
+    static bool attr[64] = {};
+    if (!attr[p->device & 63]) {
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_small_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(sizeof(double) * 2 * 64 * 64)));
+        attr[p->device & 63] = true;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    const int64_t grid = std::min<int64_t>((batch + kF64SmallWarps - 1) / kF64SmallWarps,
+                                           (int64_t)std::max(sms, 1) * 2);
+    k_small_f64<<<(unsigned)grid, 32 * kF64SmallWarps, smem, st>>>(n, x, ldx, y, ldy, batch, p->d_ct64,
+                                                                   p->d_w64);
+    note_launch(st, "k_small_f64", 16.0 * batch * n, 4.0 * (double)batch * n * n);
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
 dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
                                 int64_t ldy, int64_t batch, cudaStream_t st) {
     if (!p->d_ct64 || !p->d_w64) return DCTPLUS_ERR_UNSUPPORTED;
@@ -708,22 +881,20 @@ dctplus_status launch_dense_f64(dctplus_plan_t p, const double* x, int64_t ldx, 
     return DCTPLUS_OK;
 }
 
-// hi copy and TF32 remainder of a row-major batch (dense-GFT baseline input)
-// (hi may be null: the product then reads x itself as the hi operand)
-__global__ void k_split_rows(const float* __restrict__ x, int64_t ldx, int n, int64_t batch,
-                             float* __restrict__ hi, float* __restrict__ lo) {
+// copy of a row-major batch into a packed, 16-byte aligned buffer (the dense-GFT
+// baseline's input when x itself does not suit the tensor maps)
+__global__ void k_pack_rows(const float* __restrict__ x, int64_t ldx, int n, int64_t batch,
+                            float* __restrict__ out) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t total = batch * n;
     for (; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t b = idx / n;
         int j = (int)(idx % n);
-        float v = x[b * ldx + j];
-        if (hi) hi[idx] = v;
-        lo[idx] = tf32_lo(v);
+        out[idx] = x[b * ldx + j];
     }
 }
 
-// Per-stream scratch for the DCT output (batch x n floats, twice for split operands).
+// Per-stream scratch for the DCT output (batch x n floats).
 void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes);
 
 dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda, const float* b_hi,
@@ -737,17 +908,20 @@ dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, f
     const bool y_ok = (reinterpret_cast<uintptr_t>(y) & 15) == 0 && (ldy & 3) == 0;
     const size_t plane = (size_t)batch * n;
     if (p->cauchy_mode == DCTPLUS_CAUCHY_DENSE_GFT && y_ok) {
-        // comparison baseline: y = (x_hi + x_lo)(X^T_hi + X^T_lo)^T in one dense product;
-        // x itself is the hi operand when its layout allows, so only x_lo is written
-        const bool x_ok = (reinterpret_cast<uintptr_t>(x) & 15) == 0 && ldx == n;  // same ld as x_lo
-        float* ws = static_cast<float*>(plan_workspace(p, st, 2 * sizeof(float) * plane));
+        // comparison baseline: y = (x_hi + x_lo)(X^T_hi + X^T_lo)^T in one dense product,
+        // x_lo formed on chip; x is read in place when its layout suits the tensor maps
+        const bool x_ok = (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0;
+        if (x_ok)
+            return launch_gemm_tc(x, nullptr, ldx, p->d_xthi, p->d_xtlo, n, y, ldy, (int)batch, n, n, st,
+                                  p->device);
+        float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * plane));
         if (!ws) return DCTPLUS_ERR_CUDA;
         int64_t blocks = std::min<int64_t>((int64_t)((plane + 255) / 256), 152 * 16);
-        k_split_rows<<<(unsigned)blocks, 256, 0, st>>>(x, ldx, n, batch, x_ok ? nullptr : ws, ws + plane);
-        note_launch(st, "k_split_rows", (x_ok ? 8.0 : 12.0) * plane, 0.0);
+        k_pack_rows<<<(unsigned)blocks, 256, 0, st>>>(x, ldx, n, batch, ws);
+        note_launch(st, "k_pack_rows", 8.0 * plane, 0.0);
         DCTPLUS_CUDA_TRY(cudaGetLastError());
-        return launch_gemm_tc(x_ok ? x : ws, ws + plane, x_ok ? ldx : n, p->d_xthi, p->d_xtlo, n, y,
-                              ldy, (int)batch, n, n, st, p->device);
+        return launch_gemm_tc(ws, nullptr, n, p->d_xthi, p->d_xtlo, n, y, ldy, (int)batch, n, n, st,
+                              p->device);
     }
     if (n & (n - 1)) {
         // no FFT length: the DCT-II and the Cauchy product as CUDA-core products with the
@@ -761,17 +935,17 @@ dctplus_status launch_large_f32(dctplus_plan_t p, const float* x, int64_t ldx, f
     }
     if (p->cauchy_mode == DCTPLUS_CAUCHY_HIER && y_ok) return launch_hier(p, x, ldx, y, ldy, batch, st);
     if (p->cauchy_mode == DCTPLUS_CAUCHY_DENSE && p->d_whi && y_ok) {
-        // Algorithm 1 steps 1-2 (DCT-II, split for the tensor cores), then y = W s
-        float* ws = static_cast<float*>(plan_workspace(p, st, 2 * sizeof(float) * plane));
+        // Algorithm 1 steps 1-2 (DCT-II), then y = W s (s split on chip)
+        float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * plane));
         if (!ws) return DCTPLUS_ERR_CUDA;
-        dctplus_status r = launch_dct_fft(p, x, ldx, ws, ws + plane, n, batch, st);
+        dctplus_status r = launch_dct_fft(p, x, ldx, ws, n, batch, st);
         if (r != DCTPLUS_OK) return r;
-        return launch_gemm_tc(ws, ws + plane, n, p->d_whi, p->d_wlo, n, y, ldy, (int)batch, n, n,
-                              st, p->device);
+        return launch_gemm_tc(ws, nullptr, n, p->d_whi, p->d_wlo, n, y, ldy, (int)batch, n, n, st,
+                              p->device);
     }
     float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * plane));
     if (!ws) return DCTPLUS_ERR_CUDA;
-    dctplus_status r = launch_dct_fft(p, x, ldx, ws, nullptr, n, batch, st);
+    dctplus_status r = launch_dct_fft(p, x, ldx, ws, n, batch, st);
     if (r != DCTPLUS_OK) return r;
     return launch_cauchy_simt(p, ws, n, y, ldy, batch, st);
 }

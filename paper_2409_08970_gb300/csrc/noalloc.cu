@@ -111,7 +111,7 @@ extern "C" dctplus_status dctplus_execute_noalloc(dctplus_plan_t p, const float*
     dctplus_status st = noalloc_scratch(cur, &s);
     if (st != DCTPLUS_OK) return st;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    st = launch_dct_fft(p, x_dev, ldx, s, nullptr, n, batch, cs);
+    st = launch_dct_fft(p, x_dev, ldx, s, n, batch, cs);
     if (st != DCTPLUS_OK) return st;
     return launch_cauchy_simt(p, s, n, y_dev, ldy, batch, cs);
 }

@@ -255,22 +255,21 @@ extern "C" dctplus_status dctplus_execute_pruned(const dctplus_plan_t* plans, in
     if (st != DCTPLUS_OK) return st;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     const size_t plane = (size_t)batch * n;
-    float* s = static_cast<float*>(plan_workspace(plans[0], cs, 2 * sizeof(float) * plane));
+    float* s = static_cast<float*>(plan_workspace(plans[0], cs, sizeof(float) * plane));
     if (!s) return DCTPLUS_ERR_CUDA;
-    float* s_lo = s + plane;
 
     const bool tc = fft && width % 128 == 0 && width / 128 <= 128 && c_p % 32 == 0 &&
                     (reinterpret_cast<uintptr_t>(y_dev) & 15) == 0 && (ldy & 3) == 0;
     // Algorithm 1 step 1, once for all K updates
     if (fft) {
-        st = launch_dct_fft(plans[0], x_dev, ldx, s, tc ? s_lo : nullptr, n, batch, cs);
+        st = launch_dct_fft(plans[0], x_dev, ldx, s, n, batch, cs);
     } else {
         st = launch_rows_gemm(x_dev, ldx, plans[0]->d_ct32, n, s, n, batch, n, n, cs);
     }
     if (st != DCTPLUS_OK) return st;
     // Theorem 3.4's pruned Cauchy products of all K updates in one contraction
     if (tc)
-        return launch_gemm_tc_band(s, s_lo, n, c_p, set->b_hi, set->b_lo, c_p, y_dev, ldy,
+        return launch_gemm_tc_band(s, nullptr, n, c_p, set->b_hi, set->b_lo, c_p, y_dev, ldy,
                                    (int)batch, (int)width, c_p, nullptr, cs, cur);
     return launch_rows_gemm(s, n, set->b32, c_p, y_dev, ldy, batch, (int)width, c_p, cs);
 }

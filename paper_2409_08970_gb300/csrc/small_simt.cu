@@ -237,10 +237,6 @@ dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t l
     return launch_small_single<float>(p, x, ldx, y, ldy, batch, s);
 }
 
-dctplus_status launch_small_simt_f64(dctplus_plan_t p, const double* x, int64_t ldx, double* y,
-                                     int64_t ldy, int64_t batch, cudaStream_t s) {
-    return launch_small_single<double>(p, x, ldx, y, ldy, batch, s);
-}
 
 // -------------------------------------------------------------- grouped runs
 
