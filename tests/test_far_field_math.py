@@ -1,4 +1,5 @@
-"""The leaf-level Chebyshev far field of the hierarchical Cauchy mode, checked in FP64 on the host.
+"""The Chebyshev far field of the hierarchical Cauchy mode, checked in FP64 on the host: the
+leaf-level form (one dense leaf-to-leaf kernel matrix) and the multilevel tree the mode runs.
 
 The hierarchical mode evaluates W = X^T U (Theorem 3.1, W_rj = -a_r z_j / (mu_r - lambda_j)) as
 an exact near field (target leaf I against source leaves I-1..I+1) plus a far field
@@ -112,3 +113,112 @@ def test_interpolation_rate_with_the_degree():
         errs.append(np.abs(approx - exact).max() / np.abs(exact).max())
     assert errs[2] < 1e-8
     assert errs[0] > errs[1] > errs[2]
+
+
+# ------------------------------------------------------------------ multilevel far field
+#
+# The hierarchical mode's far field is a 1-D fast multipole tree over the angle boxes:
+# leaf moments (P2M, the factor P above) are re-expanded up the tree (M2M: the parent's
+# Lagrange basis at its children's nodes, exact for polynomials of the degree), every box
+# takes the kernel samples against the boxes of its interaction list (M2L: at least one box
+# apart, parents adjacent; at the top level of 4 boxes, every box at least one apart), and
+# the local expansions come down to the leaves (L2L, the transposed re-expansion), where the
+# targets' weights Q read them. These factors are rebuilt here from that definition.
+
+def child_reexpansion():
+    """E[k][a, b] = S_a((x_b + 2k - 1) / 2): the parent's basis at child k's nodes (k = 0 left)."""
+    t = cheb_nodes()
+    return [lagrange((t + 2 * k - 1) / 2.0).T for k in (0, 1)]
+
+
+def interaction_list(level_boxes, b, top):
+    if top:
+        return [c for c in range(level_boxes) if abs(c - b) >= 2]
+    return [c for c in (b - 3, b - 2, b + 2, b + 3)
+            if 0 <= c < level_boxes and abs(c // 2 - b // 2) <= 1]
+
+
+def multilevel_far_operator(n):
+    """Matrix F with leaf locals = F (leaf moments), both (nleaf R) long, built level by level."""
+    nleaf = n // LEAF
+    E = child_reexpansion()
+    levels = []
+    nb = nleaf
+    while nb >= 4:
+        levels.append(nb)
+        nb //= 2
+    # up: U[l] maps leaf moments to level-l moments
+    U = [np.eye(nleaf * R)]
+    for l in range(1, len(levels)):
+        nb = levels[l]
+        step = np.zeros((nb * R, levels[l - 1] * R))
+        for p in range(nb):
+            for k in (0, 1):
+                step[p * R:(p + 1) * R, (2 * p + k) * R:(2 * p + k + 1) * R] = E[k]
+        U.append(step @ U[-1])
+    F = np.zeros((nleaf * R, nleaf * R))
+    downs = [np.eye(nleaf * R)]  # downs[l] maps level-l locals to leaf locals (L2L chains)
+    for l in range(1, len(levels)):
+        nb_child, nb = levels[l - 1], levels[l]
+        step = np.zeros((nb_child * R, nb * R))
+        for c in range(nb_child):
+            step[c * R:(c + 1) * R, (c // 2) * R:(c // 2 + 1) * R] = E[c % 2].T
+        downs.append(downs[-1] @ step)
+    for l, nb in enumerate(levels):
+        h = np.pi / nb
+        nodes = (np.arange(nb)[:, None] + 0.5) * h + 0.5 * h * cheb_nodes()[None, :]
+        T = np.zeros((nb * R, nb * R))
+        top = l == len(levels) - 1
+        for b in range(nb):
+            for c in interaction_list(nb, b, top):
+                ph, tj = nodes[b][:, None], nodes[c][None, :]
+                T[b * R:(b + 1) * R, c * R:(c + 1) * R] = 1.0 / (
+                    4.0 * np.sin(0.5 * (ph + tj)) * np.sin(0.5 * (ph - tj)))
+        F += downs[l] @ T @ U[l]
+    return F
+
+
+@pytest.mark.parametrize("n", [256, 1024, 4096])
+@pytest.mark.parametrize("kind", ["dense_v", "self_loop"])
+def test_multilevel_far_field_matches_the_far_part_of_w(n, kind):
+    v, rho = (random_unit_v(n, seed=1), 2.0) if kind == "dense_v" else (self_loop_v(n, 0), -0.5)
+    plan = cauchy.make_plan(n, v, rho)
+    W = cauchy.cauchy_rows(plan, np.arange(n))
+    P, _, Q, src_leaf, tgt_leaf = far_field_factors(plan)
+    approx = Q @ (multilevel_far_operator(n) @ P)
+    far = (tgt_leaf[:, None] >= 0) & (np.abs(tgt_leaf[:, None] - src_leaf[None, :]) >= 2)
+    exact = np.where(far, W, 0.0)
+    rel = np.linalg.norm(approx - exact, axis=1) / np.linalg.norm(W, axis=1)
+    assert rel.max() < 1e-8, rel.max()
+
+
+def test_multilevel_lists_cover_each_far_leaf_pair_once():
+    """Every (target leaf, source leaf) pair at least one leaf apart meets through exactly one
+    interaction-list entry over the levels, and no nearer pair does."""
+    for nleaf in (4, 16, 64, 256):
+        levels = []
+        nb = nleaf
+        while nb >= 4:
+            levels.append(nb)
+            nb //= 2
+        count = np.zeros((nleaf, nleaf), dtype=int)
+        for l, nb in enumerate(levels):
+            top = l == len(levels) - 1
+            for b in range(nb):
+                for c in interaction_list(nb, b, top):
+                    count[b << l:(b + 1) << l, c << l:(c + 1) << l] += 1
+        i, j = np.meshgrid(np.arange(nleaf), np.arange(nleaf), indexing="ij")
+        assert np.array_equal(count, (np.abs(i - j) >= 2).astype(int)), nleaf
+
+
+def test_reexpansion_is_exact_for_the_parent_basis():
+    """M2M loses nothing: the parent's basis restricted to a child is reproduced by the child's
+    interpolant (a polynomial of the same degree)."""
+    E = child_reexpansion()
+    t = cheb_nodes()
+    u = np.linspace(-1, 1, 33)
+    for k in (0, 1):
+        x_parent = (u + 2 * k - 1) / 2.0          # child's [-1, 1] mapped into the parent
+        direct = lagrange(x_parent)               # S_a^parent at those points
+        via_child = lagrange(u) @ E[k].T          # child's basis times re-expansion
+        assert np.abs(direct - via_child).max() < 1e-11
