@@ -68,7 +68,9 @@ typedef enum {
     DCTPLUS_CAUCHY_AUTO = 0,  /* pick by n */
     DCTPLUS_CAUCHY_DENSE = 1, /* dense split-TF32 tensor-core product with the plan's
                                  W = diag(a) C(mu, lambda) diag(z) table; n % 128 == 0, n <= 4096 */
-    DCTPLUS_CAUCHY_HIER = 2,  /* near-field band + leaf-level Chebyshev far field (Theorem 3.2's fast-product family) */
+    DCTPLUS_CAUCHY_HIER = 2,  /* near-field band + Chebyshev far field, leaf level or a multipole
+                                 tree (Theorem 3.2's fast-product family); n a power of two,
+                                 256 <= n <= 16384 */
     DCTPLUS_CAUCHY_SIMT = 3,  /* CUDA-core product, W from a stored table (n <= 4096) or
                                  generated tile by tile in shared memory */
     DCTPLUS_CAUCHY_DENSE_GFT = 4, /* comparison baseline, not the factored method: one dense
@@ -88,7 +90,11 @@ typedef enum {
 typedef struct {
     int cauchy_mode;      /* dctplus_cauchy_mode; 0 = auto */
     int max_secular_iter; /* cap on root iterations per root; 0 = 200 */
-    int hier_rank;        /* reserved and ignored (the far field uses degree 12) */
+    int far_field;        /* hierarchical mode's far field: 0 = default (the tree from n = 8192),
+                             1 = leaf level (one dense product with the leaf-to-leaf kernel
+                             samples: (12 n / 64)^2 tensor-core multiply-adds per signal,
+                             2 (12 n / 64)^2 floats of tables), 2 = multipole tree (M2M, M2L,
+                             L2L over the angle boxes: O(n log n) work, O(n) tables) */
     int device;           /* CUDA device ordinal; -1 = current device */
 } dctplus_opts;
 
@@ -128,6 +134,9 @@ int dctplus_plan_size(dctplus_plan_t plan);
 
 /* The Cauchy evaluation the plan uses for FP32 execute (a dctplus_cauchy_mode). */
 int dctplus_plan_cauchy_mode(dctplus_plan_t plan);
+
+/* The far-field form of a hierarchical plan (1 = leaf level, 2 = tree), 0 otherwise. */
+int dctplus_plan_far_field(dctplus_plan_t plan);
 
 /* --------------------------------------------------------------- forward */
 

@@ -167,15 +167,20 @@ class Plan:
     """A Fast DCT+ plan: the GFT of L~ + rho v v^T for signals of length n."""
 
     def __init__(self, n: int, v, rho: float, cauchy_mode: int = CAUCHY_AUTO,
-                 max_secular_iter: int = 0, hier_rank: int = 0, device: int = -1):
+                 max_secular_iter: int = 0, far_field: int = 0, device: int = -1):
         self.n = int(n)
         self.rho = float(rho)
-        opts = Opts(cauchy_mode, max_secular_iter, hier_rank, device)
+        opts = Opts(cauchy_mode, max_secular_iter, far_field, device)
         self.handle = dctplus_plan(self.n, v, self.rho, opts)
 
     @property
     def cauchy_mode(self) -> int:
         return int(_lib.load().dctplus_plan_cauchy_mode(self.handle))
+
+    @property
+    def far_field(self) -> int:
+        """Far-field form of a hierarchical plan: 1 = leaf level, 2 = tree (0 otherwise)."""
+        return int(_lib.load().dctplus_plan_far_field(self.handle))
 
     def inspect(self) -> dict:
         return dctplus_plan_inspect(self.handle, self.n)

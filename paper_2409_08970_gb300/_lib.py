@@ -36,7 +36,7 @@ SEG_WORDS = 3
 # every symbol include/dctplus.h declares
 EXPORTS = (
     "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect", "dctplus_plan_size",
-    "dctplus_plan_cauchy_mode", "dctplus_execute", "dctplus_execute_host",
+    "dctplus_plan_cauchy_mode", "dctplus_plan_far_field", "dctplus_execute", "dctplus_execute_host",
     "dctplus_execute_noalloc", "dctplus_execute_pruned", "dctplus_backward",
     "dctplus_group_create", "dctplus_group_destroy", "dctplus_execute_group",
     "dctplus_execute_group_host", "dctplus_sync_check", "dctplus_launch_count",
@@ -53,7 +53,7 @@ class DctPlusError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("cauchy_mode", ctypes.c_int), ("max_secular_iter", ctypes.c_int),
-                ("hier_rank", ctypes.c_int), ("device", ctypes.c_int)]
+                ("far_field", ctypes.c_int), ("device", ctypes.c_int)]
 
 
 _lib = None
@@ -74,6 +74,7 @@ def load():
         "dctplus_plan_inspect": (c_int, [vp, vp, vp, vp, vp, vp, vp]),
         "dctplus_plan_size": (c_int, [vp]),
         "dctplus_plan_cauchy_mode": (c_int, [vp]),
+        "dctplus_plan_far_field": (c_int, [vp]),
         "dctplus_execute": (c_int, [vp, c_int, vp, i64, vp, i64, i64, vp]),
         "dctplus_execute_host": (c_int, [vp, c_int, vp, vp, i64, vp]),
         "dctplus_execute_noalloc": (c_int, [vp, vp, i64, vp, i64, i64, vp]),

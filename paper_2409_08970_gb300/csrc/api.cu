@@ -290,7 +290,8 @@ dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, do
     dctplus_opts o{};
     o.device = -1;
     if (opts) o = *opts;
-    if (o.cauchy_mode < 0 || o.cauchy_mode > DCTPLUS_CAUCHY_NFST || o.max_secular_iter < 0)
+    if (o.cauchy_mode < 0 || o.cauchy_mode > DCTPLUS_CAUCHY_NFST || o.max_secular_iter < 0 ||
+        o.far_field < 0 || o.far_field > 2)
         return DCTPLUS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DCTPLUS_ERR_NO_DEVICE;
@@ -308,6 +309,7 @@ dctplus_status dctplus_plan(dctplus_plan_t* out, int n, const double* v_host, do
     p->device = dev;
     p->v.assign(v_host, v_host + n);
     p->cauchy_mode = o.cauchy_mode;
+    p->far_field = o.far_field;
     dctplus_status st = build_plan(p, o);
     if (st != DCTPLUS_OK) {
         free_plan_tables(p);
@@ -334,6 +336,10 @@ void dctplus_destroy(dctplus_plan_t p) {
 int dctplus_plan_size(dctplus_plan_t p) { return p ? p->n : -1; }
 
 int dctplus_plan_cauchy_mode(dctplus_plan_t p) { return p ? p->cauchy_mode : -1; }
+
+int dctplus_plan_far_field(dctplus_plan_t p) {
+    return p && p->cauchy_mode == DCTPLUS_CAUCHY_HIER ? p->far_field : 0;
+}
 
 dctplus_status dctplus_plan_inspect(dctplus_plan_t p, double* eigenvalues, double* z,
                                     int* row_kind, int* row_pole, double* row_tau,

@@ -16,22 +16,27 @@
 //               entries of W, a band matrix applied on the tensor cores with
 //               the split-TF32 GEMM (each 128-row output tile contracts a
 //               K window of s against a compact [n x Kw] slab of W entries);
-//   far field   every other source, through Chebyshev interpolation of degree
-//               R in both variables at the leaf level: P2M (per leaf, the
-//               sources' z-weighted interpolation coefficients, CUDA cores),
-//               then one dense product with the kernel sampled at the leaf
-//               nodes of every well-separated leaf pair (target leaf I,
-//               source leaf J, |I - J| >= 2), a [nleaf R x nleaf R] matrix on
-//               the tensor cores (split-TF32 GEMM), then L2P (-a folded into
-//               the weights, CUDA cores) added into y. A single level with a
-//               dense leaf-to-leaf operator trades a multilevel tree's O(n)
-//               translation work for (12 n / 64)^2 tensor-core multiply-adds
-//               per signal, fewer than the dense product's n^2 by (64 / 12)^2,
-//               and needs no barriers between tree levels.
+//   far field   every other source, through a 1-D fast multipole tree over the
+//               th-boxes with Chebyshev interpolation of degree R in both
+//               variables: P2M (leaf moments, the sources' z-weighted Lagrange
+//               weights; in the DCT kernel, a split-TF32 contraction), M2M
+//               (the parent's Lagrange basis at its children's nodes, exact
+//               for polynomials of the degree; each level composed from its
+//               leaves, so the levels are independent), M2L per level (the
+//               kernel sampled at the nodes of each box against the boxes of
+//               its interaction list: at least one box apart, parents
+//               adjacent; at the top level of 4 boxes, every box at least one
+//               apart), L2L chains down to the leaves, and L2P (-a folded into
+//               the weights) as extra K columns of the output product. Every
+//               far leaf pair meets in exactly one list, so the far field is
+//               the leaf-level one, evaluated in O(n log n) multiply-adds with
+//               O(n) tables. M2M, M2L and L2L are 12 x 12 blocks per signal;
+//               they run in FP32 on the CUDA cores, a lane per signal, each
+//               block broadcast from shared memory or L1.
 // Roots outside [0, 4] (at most the largest for rho > 0 or the smallest for
 // rho < 0; the paper's pre-processing isolates the same root) have no real
-// angle; their rows are dense dot products, formed as per-leaf partial sums
-// by P2M and summed by L2P.
+// angle; their rows are dense dot products, formed by the DCT kernel from the
+// same z-weighted coefficients and placed after the leaf-local coefficients.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,23 +52,35 @@ constexpr int kR = 12;  // Chebyshev degree of the far-field expansions
 
 struct HierTables {
     int nleaf = 0, Kw = 0;
-    int nc = 0, ncp = 0;         // leaf coefficients nleaf R, padded to a multiple of 128
-    int ldl = 0;                 // row pitch of the leaf-local array: ncp + 32 (dense-row slots)
+    int form = 0;                // far field: 1 = leaf level (one dense leaf-to-leaf product), 2 = tree
+    int nc = 0;                  // leaf-local coefficients nleaf R
+    int ncp = 0;                 // nc rounded up to 128 (the leaf-to-leaf product's output width)
+    int dslot = 0;               // column of the dense-row slots in the leaf-local array
+    int ldl = 0;                 // row pitch of the leaf-local array: dslot + 32
+    int ldm = 0;                 // row pitch of the moment (and M2L output) arrays
     int Kx = 0;                  // far-field (L2P) columns per 128-row output tile, multiple of 32
+    int nlev = 0, nbox = 0;      // tree levels (leaf level included) and boxes over all levels
+    int lev_off[kFarMaxLev] = {}, box_off[kFarMaxLev + 1] = {}, chain_off[kFarMaxLev] = {};
     std::vector<int> kbeg;       // per 128-row output tile: first source of the K window
     float* slab_hi = nullptr;    // n x Kw
     float* slab_lo = nullptr;
     float* zf = nullptr;         // n: z_j (0 where deflated)
     float* tq_hi = nullptr;      // 64 x kFarTqLd: S_a at the 64 source positions of any leaf
     float* tq_lo = nullptr;
+    float* tm_hi = nullptr;      // 24 x kFarTqLd: M2M re-expansion of both children (tree)
+    float* tm_lo = nullptr;
+    float* kf_hi = nullptr;      // ncp x ncp: leaf-to-leaf kernel samples, TF32 hi and lo (leaf
+    float* kf_lo = nullptr;      //   level; zero for near pairs and padding)
+    int* tab_l2l = nullptr;      // its K-segment table
+    int64_t chunks_l2l = 0;
+    float* m2l = nullptr;        // nbox x 4 slots x [12][12]: M2L kernel samples (FP32, tree)
+    int* slot_box = nullptr;     // nbox x 4: source box (within its level) of each slot, -1 if none
+    float* chain = nullptr;      // L2L chains, level l >= 1, leaf position i < 2^l: [12][12] each
     int* row_leaf = nullptr;     // n
     float* ext_hi = nullptr;     // n x (Kx + 32): L2P weights -a_r S_a(u_r) against the leaf-local
     float* ext_lo = nullptr;     //   coefficients of the row's tile window, then the dense-row slots
-    float* kf_hi = nullptr;      // ncp x ncp: leaf-to-leaf kernel samples, TF32 hi
-    float* kf_lo = nullptr;      //            and lo (zero for near pairs and padding)
-    int* tab_l2l = nullptr;      // K-segment tables of the leaf-to-leaf and the output products
-    int* tab_out = nullptr;
-    int64_t chunks_l2l = 0, chunks_out = 0;
+    int* tab_out = nullptr;      // K-segment table of the output product
+    int64_t chunks_out = 0;
     double acols_out = 0.0;
     int nout = 0;
     int out_row[2] = {-1, -1};
@@ -132,8 +149,9 @@ __global__ void k_band_slab(int n, int Kw, const int* kbeg_tile, const int* row_
 
 void free_hier(HierTables* h) {
     if (!h) return;
-    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf,     h->tq_hi,   h->tq_lo,   h->row_leaf, h->ext_hi,
-                    h->ext_lo,  h->kf_hi,   h->kf_lo, h->tab_l2l, h->tab_out, h->out_g};
+    void* ptrs[] = {h->slab_hi, h->slab_lo, h->zf,     h->tq_hi,  h->tq_lo,   h->tm_hi, h->tm_lo,
+                    h->kf_hi,   h->kf_lo,   h->tab_l2l, h->m2l,   h->slot_box, h->chain, h->row_leaf,
+                    h->ext_hi,  h->ext_lo,  h->tab_out, h->out_g};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
@@ -144,6 +162,8 @@ bool hier_shape(int n) { return n >= 4 * kLeaf && (n & (n - 1)) == 0 && n <= kMa
 dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     const int n = p->n;
     if (!hier_shape(n)) return DCTPLUS_ERR_UNSUPPORTED;
+    const int form = p->far_field;
+    if (form != 1 && form != 2) return DCTPLUS_ERR_INVALID_ARG;
     HierTables* h = new HierTables();
     p->hier = h;
     h->nleaf = n / kLeaf;
@@ -213,11 +233,13 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
             tq_lo[(size_t)jj * kFarTqLd + a] = tf32_host((float)(v - (double)hi));
         }
     }
-    // leaf-local array per signal: nleaf R coefficients (leaf I at I R), padding to
-    // ncp, then 32 slots of which the first nout hold the dense rows' values
+    // leaf-local array per signal: nleaf R coefficients (leaf I at I R), then 32
+    // slots of which the first nout hold the dense rows' values
     h->nc = nleaf * kR;
     h->ncp = (h->nc + 127) / 128 * 128;
-    h->ldl = h->ncp + 32;
+    h->form = form;
+    h->dslot = form == 1 ? h->ncp : h->nc;  // the leaf-to-leaf product writes all ncp columns
+    h->ldl = h->dslot + 32;
     // L2P weights of each far-field target row against the leaf-local coefficients of
     // its tile's window (leaves lmin .. lmax of the tile, starting at column lmin R)
     int kx = 0;
@@ -268,7 +290,7 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         }
         const int xw = (tile_lmax[t] - tile_lmin[t] + 1) * kR;
         if (far) add(1, tile_lmin[t] * kR, 0, (xw + 31) / 32);  // far field: L2P of the leaf window
-        if (dense) add(1, h->ncp, h->Kx, 1);                    // dense rows: their values
+        if (dense) add(1, h->dslot, h->Kx, 1);                  // dense rows: their values
         e[0] = nseg;
         e[1] = nk;
         h->chunks_out += nk;
@@ -276,23 +298,102 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
                         (dense ? 32.0 : 0.0);
     }
     h->acols_out = std::min(h->acols_out, (double)n + h->ldl);
-    std::vector<int> tab_l2l((size_t)(h->ncp / 128) * kGemmTabStride, 0);
-    for (int t = 0; t < h->ncp / 128; ++t) {
-        int* e = &tab_l2l[(size_t)t * kGemmTabStride];
-        e[0] = 1;
-        e[1] = (h->nc + 31) / 32;  // columns past nc of K_far are zero
-        e[2] = 0;
-        e[3] = 0;
-        e[4] = 0;
-        e[5] = (h->nc + 31) / 32;
+
+    // the tree (its levels are also counted for the leaf-level form, which uses none of
+    // the tables below): level l has nleaf >> l boxes of th-width pi / (nleaf >> l), down to 4 boxes
+    h->nlev = 0;
+    h->nbox = 0;
+    for (int nb = nleaf; nb >= 4; nb >>= 1) {
+        if (h->nlev >= kFarMaxLev) return DCTPLUS_ERR_UNSUPPORTED;
+        h->box_off[h->nlev] = h->nbox;
+        h->lev_off[h->nlev] = h->nbox * kR;
+        h->nbox += nb;
+        ++h->nlev;
     }
-    h->chunks_l2l = (int64_t)(h->ncp / 128) * ((h->nc + 31) / 32);
-    // leaf-to-leaf kernel 1 / (mu - lambda) = 1 / (2 cos th - 2 cos ph) at the
-    // Chebyshev nodes of target leaf I (ph) and source leaf J (th), |I - J| >= 2;
-    // rows (I, a), columns (J, b), zero-padded to ncp x ncp
-    const int nc = h->nc, ncp = h->ncp;
-    std::vector<float> kf_hi((size_t)ncp * ncp, 0.0f), kf_lo((size_t)ncp * ncp, 0.0f);
-    {
+    h->box_off[h->nlev] = h->nbox;
+    h->ldm = form == 2 ? h->nbox * kR : h->nc;  // multiples of 4
+    // M2M re-expansion: E_k[a][b] = S_a((x_b + 2k - 1) / 2), the parent's basis at child
+    // k's nodes (only through the chains below: up the tree the composed re-expansion is
+    // the transposed chain)
+    double E[2][kR][kR];
+    for (int k = 0; k < 2; ++k)
+        for (int a = 0; a < kR; ++a)
+            for (int b = 0; b < kR; ++b) E[k][a][b] = cheb_lagrange(a, (cheb_node(b) + 2 * k - 1) / 2.0);
+    // as the DCT kernel's M2M operand: row k = child * 12 + b, column a, TF32 hi / lo
+    std::vector<float> tm_hi((size_t)24 * kFarTqLd, 0.0f), tm_lo((size_t)24 * kFarTqLd, 0.0f);
+    for (int k = 0; k < 2; ++k)
+        for (int b = 0; b < kR; ++b)
+            for (int a = 0; a < kR; ++a) {
+                const double v = E[k][a][b];
+                const size_t at = (size_t)(k * kR + b) * kFarTqLd + a;
+                tm_hi[at] = tf32_host((float)v);
+                tm_lo[at] = tf32_host((float)(v - (double)tm_hi[at]));
+            }
+    // M2L: per box B of level l and slot s (source box B + {-3, -2, 2, 3}[s] if it is in
+    // B's interaction list), block [a][b] = 1 / (mu - lambda) at (ph_a of B, th_b of C)
+    static const int kSlotOff[4] = {-3, -2, 2, 3};
+    std::vector<float> m2l((size_t)h->nbox * 4 * kR * kR, 0.0f);
+    std::vector<int> slot_box((size_t)h->nbox * 4, -1);
+    for (int l = 0; l < h->nlev; ++l) {
+        const int nb = nleaf >> l;
+        const bool top = l == h->nlev - 1;
+        const double hb = M_PI / nb, hw = 0.5 * hb;
+        for (int B = 0; B < nb; ++B) {
+            for (int sl = 0; sl < 4; ++sl) {
+                const int Cb = B + kSlotOff[sl];
+                if (Cb < 0 || Cb >= nb) continue;
+                if (!top && std::abs(Cb / 2 - B / 2) > 1) continue;
+                const size_t e = (size_t)(h->box_off[l] + B) * 4 + sl;
+                slot_box[e] = Cb;
+                for (int b = 0; b < kR; ++b) {
+                    const double th = (Cb + 0.5) * hb + hw * cheb_node(b);
+                    for (int a = 0; a < kR; ++a) {
+                        const double phi = (B + 0.5) * hb + hw * cheb_node(a);
+                        const double v = 1.0 / (4.0 * std::sin(0.5 * (phi + th)) * std::sin(0.5 * (phi - th)));
+                        m2l[(e * kR + a) * kR + b] = (float)v;
+                    }
+                }
+            }
+        }
+    }
+    // L2L chains: level-l local expansion of the ancestor to leaf I, I mod 2^l = i:
+    // G = E_{b1}^T E_{b2}^T ... E_{bl}^T with b_m = (i >> (m - 1)) & 1, stored [a][b]
+    int nchain = 0;
+    for (int l = 1; l < h->nlev; ++l) {
+        h->chain_off[l] = nchain;
+        nchain += 1 << l;
+    }
+    std::vector<float> chain((size_t)std::max(nchain, 1) * kR * kR, 0.0f);
+    for (int l = 1; l < h->nlev; ++l) {
+        for (int i = 0; i < (1 << l); ++i) {
+            double G[kR][kR], T[kR][kR];
+            for (int a = 0; a < kR; ++a)
+                for (int b = 0; b < kR; ++b) G[a][b] = a == b ? 1.0 : 0.0;
+            for (int m = 1; m <= l; ++m) {  // G <- G E_{b_m}^T
+                const int bm = (i >> (m - 1)) & 1;
+                for (int a = 0; a < kR; ++a)
+                    for (int b = 0; b < kR; ++b) {
+                        double acc = 0.0;
+                        for (int c = 0; c < kR; ++c) acc += G[a][c] * E[bm][b][c];
+                        T[a][b] = acc;
+                    }
+                std::memcpy(G, T, sizeof(G));
+            }
+            const size_t e = (size_t)(h->chain_off[l] + i);
+            for (int a = 0; a < kR; ++a)
+                for (int b = 0; b < kR; ++b) chain[(e * kR + a) * kR + b] = (float)G[a][b];
+        }
+    }
+
+    // leaf level: the kernel 1 / (mu - lambda) = 1 / (2 cos th - 2 cos ph) at the
+    // Chebyshev nodes of target leaf I (ph) and source leaf J (th), |I - J| >= 2; rows
+    // (I, a), columns (J, b), zero-padded to ncp x ncp, and its segment table
+    std::vector<float> kf_hi, kf_lo;
+    std::vector<int> tab_l2l;
+    if (form == 1) {
+        const int nc = h->nc, ncp = h->ncp;
+        kf_hi.assign((size_t)ncp * ncp, 0.0f);
+        kf_lo.assign((size_t)ncp * ncp, 0.0f);
         const double hw = 0.5 * hleaf;
         std::vector<double> node(nc);
         for (int I = 0; I < nleaf; ++I)
@@ -310,6 +411,14 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
                 kf_lo[(size_t)ia * ncp + jb] = tf32_host((float)(v - (double)hi));
             }
         }
+        tab_l2l.assign((size_t)(ncp / 128) * kGemmTabStride, 0);
+        for (int t = 0; t < ncp / 128; ++t) {
+            int* e = &tab_l2l[(size_t)t * kGemmTabStride];
+            e[0] = 1;
+            e[1] = (nc + 31) / 32;  // columns past nc of the kernel samples are zero
+            e[5] = (nc + 31) / 32;
+        }
+        h->chunks_l2l = (int64_t)(ncp / 128) * ((nc + 31) / 32);
     }
     // dense rows for eigenvalues outside [0, 4]: W_oj = g_oj z_j with g_oj = -a_o / (mu_o - lambda_j)
     std::vector<float> outg((size_t)std::max(h->nout, 1) * n, 0.0f);
@@ -331,10 +440,18 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     DCTPLUS_CUDA_TRY(up(&h->ext_hi, ext_hi));
     DCTPLUS_CUDA_TRY(up(&h->ext_lo, ext_lo));
     DCTPLUS_CUDA_TRY(up(&h->tab_out, tab_out));
-    DCTPLUS_CUDA_TRY(up(&h->tab_l2l, tab_l2l));
+    if (form == 2) {
+        DCTPLUS_CUDA_TRY(up(&h->tm_hi, tm_hi));
+        DCTPLUS_CUDA_TRY(up(&h->tm_lo, tm_lo));
+        DCTPLUS_CUDA_TRY(up(&h->m2l, m2l));
+        DCTPLUS_CUDA_TRY(up(&h->slot_box, slot_box));
+        DCTPLUS_CUDA_TRY(up(&h->chain, chain));
+    } else {
+        DCTPLUS_CUDA_TRY(up(&h->kf_hi, kf_hi));
+        DCTPLUS_CUDA_TRY(up(&h->kf_lo, kf_lo));
+        DCTPLUS_CUDA_TRY(up(&h->tab_l2l, tab_l2l));
+    }
     DCTPLUS_CUDA_TRY(up(&h->row_leaf, row_leaf));
-    DCTPLUS_CUDA_TRY(up(&h->kf_hi, kf_hi));
-    DCTPLUS_CUDA_TRY(up(&h->kf_lo, kf_lo));
     DCTPLUS_CUDA_TRY(up(&h->out_g, outg));
 
     int* d_kbeg = nullptr;
@@ -353,21 +470,134 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     return DCTPLUS_OK;
 }
 
+// ------------------------------------------------------------- far field tree
+
+// Device view of the tree tables (FP32; the tree runs on the CUDA cores with a lane
+// per signal, each 12 x 12 block broadcast from shared memory or L1).
+struct FarTree {
+    const float* m2l;    // nbox x 4 slots x [12 a][12 b]: kernel samples K(ph_a of B, th_b of C)
+    const int* slot_box; // nbox x 4: source box of each slot (within its level), -1 if none
+    const float* chain;  // L2L chains [a][b], level l >= 1, leaf position i < 2^l at chain_off[l] + i
+    int nlev, nbox;
+    int lev_off[kFarMaxLev];
+    int box_off[kFarMaxLev + 1];
+    int chain_off[kFarMaxLev];
+};
+
+constexpr int kTreeThreads = 256;  // signals per CTA (a lane each)
+
+__device__ __forceinline__ void load12(float (&m)[kR], const float* p) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float4 v = __ldg(q + i);
+        m[4 * i] = v.x;
+        m[4 * i + 1] = v.y;
+        m[4 * i + 2] = v.z;
+        m[4 * i + 3] = v.w;
+    }
+}
+
+__device__ __forceinline__ void store12(float* p, const float (&m)[kR]) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q[i] = make_float4(m[4 * i], m[4 * i + 1], m[4 * i + 2], m[4 * i + 3]);
+}
+
+// acc[a] += sum_b T[a][b] m[b] (trans: T[b][a]) for a 12 x 12 block T read as float4 rows
+// at a warp-uniform address (a broadcast)
+template <bool kTrans>
+__device__ __forceinline__ void block12(float (&acc)[kR], const float* T, const float (&m)[kR]) {
+    const float4* t4 = reinterpret_cast<const float4*>(T);
+    if (!kTrans) {
+#pragma unroll
+        for (int a = 0; a < kR; ++a)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float4 t = t4[a * 3 + q];
+                acc[a] = fmaf(t.x, m[4 * q], fmaf(t.y, m[4 * q + 1], fmaf(t.z, m[4 * q + 2], fmaf(t.w, m[4 * q + 3], acc[a]))));
+            }
+    } else {
+#pragma unroll
+        for (int b = 0; b < kR; ++b)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float4 t = t4[b * 3 + q];  // T[b][4q .. 4q + 3]
+                acc[4 * q] = fmaf(t.x, m[b], acc[4 * q]);
+                acc[4 * q + 1] = fmaf(t.y, m[b], acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(t.z, m[b], acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(t.w, m[b], acc[4 * q + 3]);
+            }
+    }
+}
+
+// M2L: for every box B of every level, the local expansion
+// v^l[B] = sum over B's interaction list of K(l, B, C) M^l[C].
+// CTA = (box, kTreeThreads signals); the box's slot blocks are staged in shared memory.
+__global__ void __launch_bounds__(kTreeThreads) k_far_m2l(const FarTree T, const float* __restrict__ mc,
+                                                          float* __restrict__ vv, int64_t ldm, int64_t batch) {
+    __shared__ __align__(16) float tk[4 * kR * kR];
+    __shared__ int cbox[4];
+    const int bg = blockIdx.x;
+    int l = 0;
+    while (l + 1 < T.nlev && bg >= T.box_off[l + 1]) ++l;
+    const int B = bg - T.box_off[l];
+    if (threadIdx.x < 4) cbox[threadIdx.x] = __ldg(T.slot_box + bg * 4 + threadIdx.x);
+    for (int e = threadIdx.x; e < 4 * kR * kR; e += blockDim.x) tk[e] = __ldg(T.m2l + (size_t)bg * 4 * kR * kR + e);
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.y * kTreeThreads + threadIdx.x;
+    if (s >= batch) return;
+    float acc[kR] = {};
+    const float* row = mc + s * ldm + T.lev_off[l];
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+        const int Cb = cbox[sl];
+        if (Cb < 0) continue;  // uniform across the CTA
+        float m[kR];
+        load12(m, row + (int64_t)Cb * kR);
+        block12<false>(acc, tk + sl * kR * kR, m);
+    }
+    store12(vv + s * ldm + T.lev_off[l] + (int64_t)B * kR, acc);
+}
+
+// L2L down to the leaves: leaf-local coefficients L[I] = v^0[I] + sum over the upper
+// levels l of G(l, I mod 2^l) v^l[I >> l], into the leaf-local array the output
+// product reads (leaf I at I R). CTA = (leaf, kTreeThreads signals).
+__global__ void __launch_bounds__(kTreeThreads) k_far_down(const FarTree T, const float* __restrict__ vv,
+                                                           int64_t ldm, float* __restrict__ lc, int64_t ldl,
+                                                           int64_t batch) {
+    const int I = blockIdx.x;
+    const int64_t s = (int64_t)blockIdx.y * kTreeThreads + threadIdx.x;
+    if (s >= batch) return;
+    const float* row = vv + s * ldm;
+    float acc[kR];
+    load12(acc, row + (int64_t)I * kR);
+#pragma unroll 1
+    for (int l = 1; l < T.nlev; ++l) {
+        float m[kR];
+        load12(m, row + T.lev_off[l] + (int64_t)(I >> l) * kR);
+        block12<false>(acc, T.chain + (size_t)(T.chain_off[l] + (I & ((1 << l) - 1))) * kR * kR, m);
+    }
+    store12(lc + s * ldl + (int64_t)I * kR, acc);
+}
+
 // ------------------------------------------------------------- execute
 
 void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes);
 
-// Three launches per batch:
-//   1. DCT-II (k_dct_far): s, the leaf moments (P2M) and the dense rows' values,
-//      which go to the dense-row slots of the leaf-local array (the slots after
-//      them are zeroed);
-//   2. leaf-to-leaf product (split-TF32 GEMM): leaf-local coefficients
-//      L = M K_far^T, into the leaf-local array;
+// Per batch:
+//   1. DCT-II (k_dct_far): s, the leaf moments (P2M), for the tree also the upper
+//      levels' moments (M2M), and the dense rows' values, which go to the dense-row
+//      slots of the leaf-local array (the slots after them are zeroed);
+//   2. far field to the leaf-local coefficients: the leaf-level form is one
+//      split-TF32 GEMM with the leaf-to-leaf kernel samples; the tree is M2L
+//      (k_far_m2l, every box's local expansion from its interaction list), then L2L
+//      (k_far_down, summed down the chains to the leaves);
 //   3. output product (split-TF32 GEMM over K segments): per 128-row tile the
 //      band of W against its window of s (near field), then the L2P weights
 //      against the tile's window of leaf-local coefficients (far field), then
 //      the dense rows' slots; y is written once.
-// The TF32 remainders of s, M and L are formed on chip by the GEMM.
+// The TF32 remainders of every GEMM operand are formed on chip.
 dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
                            int64_t batch, cudaStream_t st) {
     HierTables* h = p->hier;
@@ -375,28 +605,59 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     if (!h || batch > INT32_MAX || (reinterpret_cast<uintptr_t>(y) & 15) || (ldy & 3))
         return DCTPLUS_ERR_UNSUPPORTED;
     if (batch <= 0) return DCTPLUS_OK;
-    const size_t plane = (size_t)batch * n, cplane = (size_t)batch * h->ncp, lplane = (size_t)batch * h->ldl;
-    float* ws = static_cast<float*>(plan_workspace(p, st, sizeof(float) * (plane + cplane + lplane)));
+    const bool tree = h->form == 2;
+    const size_t plane = (size_t)batch * n, mplane = (size_t)batch * h->ldm, lplane = (size_t)batch * h->ldl;
+    float* ws = static_cast<float*>(
+        plan_workspace(p, st, sizeof(float) * (plane + (tree ? 2 : 1) * mplane + lplane)));
     if (!ws) return DCTPLUS_ERR_CUDA;
     float* s_hi = ws;
     float* mc = ws + plane;
-    float* lc = mc + cplane;
+    float* vv = tree ? mc + mplane : nullptr;
+    float* lc = mc + (tree ? 2 : 1) * mplane;
     DctFar far;
     far.zf = h->zf;
     far.tq_hi = h->tq_hi;
     far.tq_lo = h->tq_lo;
     far.mc = mc;
-    far.ldm = h->ncp;
+    far.ldm = h->ldm;
+    far.tm_hi = h->tm_hi;
+    far.tm_lo = h->tm_lo;
+    far.nlev = tree ? h->nlev : 1;
+    for (int l = 0; l < kFarMaxLev; ++l) far.lev_off[l] = h->lev_off[l];
     far.out_g = h->out_g;
     far.nout = h->nout;
-    far.dv = lc + h->ncp;
+    far.dv = lc + h->dslot;
     far.ldd = h->ldl;
     dctplus_status r = launch_dct_far(p, x, ldx, s_hi, n, batch, far, st);
     if (r != DCTPLUS_OK) return r;
-    GemmSrc l2l{mc, nullptr, h->ncp, h->nc, h->kf_hi, h->kf_lo, h->ncp, h->ncp};
-    r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l, (double)h->nc, lc, nullptr, h->ldl,
-                            (int)batch, h->ncp, st, p->device, "k_gemm_tc");
-    if (r != DCTPLUS_OK) return r;
+    if (!tree) {
+        GemmSrc l2l{mc, nullptr, h->ldm, h->nc, h->kf_hi, h->kf_lo, h->ncp, h->ncp};
+        r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l, (double)h->nc, lc, nullptr, h->ldl,
+                                (int)batch, h->ncp, st, p->device, "k_gemm_tc");
+        if (r != DCTPLUS_OK) return r;
+    } else {
+        FarTree T;
+        T.m2l = h->m2l;
+        T.slot_box = h->slot_box;
+        T.chain = h->chain;
+        T.nlev = h->nlev;
+        T.nbox = h->nbox;
+        for (int l = 0; l < kFarMaxLev; ++l) {
+            T.lev_off[l] = h->lev_off[l];
+            T.chain_off[l] = h->chain_off[l];
+        }
+        for (int l = 0; l <= kFarMaxLev; ++l) T.box_off[l] = h->box_off[l];
+        const int64_t gy = (batch + kTreeThreads - 1) / kTreeThreads;
+        if (gy > 65535) return DCTPLUS_ERR_UNSUPPORTED;
+        k_far_m2l<<<dim3((unsigned)h->nbox, (unsigned)gy), kTreeThreads, 0, st>>>(T, mc, vv, h->ldm, batch);
+        note_launch(st, "k_far_m2l", 8.0 * (double)batch * h->ldm, 2.0 * kR * kR * 3.5 * h->nbox * (double)batch);
+        DCTPLUS_CUDA_TRY(cudaGetLastError());
+        k_far_down<<<dim3((unsigned)h->nleaf, (unsigned)gy), kTreeThreads, 0, st>>>(T, vv, h->ldm, lc, h->ldl,
+                                                                                    batch);
+        note_launch(st, "k_far_down", 4.0 * (double)batch * (h->ldm + h->nc),
+                    2.0 * kR * kR * (h->nlev - 1) * h->nleaf * (double)batch);
+        DCTPLUS_CUDA_TRY(cudaGetLastError());
+    }
     GemmSrc out[2] = {{s_hi, nullptr, n, n, h->slab_hi, h->slab_lo, h->Kw, h->Kw},
                       {lc, nullptr, h->ldl, h->ldl, h->ext_hi, h->ext_lo, h->Kx + 32, h->Kx + 32}};
     return launch_gemm_tc_segs(out, 2, h->tab_out, h->chunks_out, h->acols_out, y, nullptr, ldy,

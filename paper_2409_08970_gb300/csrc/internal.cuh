@@ -56,6 +56,7 @@ struct dctplus_plan_s {
     double rho = 0.0;
     int device = 0;
     int cauchy_mode = DCTPLUS_CAUCHY_AUTO;
+    int far_field = 0;  // hierarchical mode: 1 = leaf level, 2 = tree (resolved at plan time)
     std::vector<double> v;
 
     // host copies of the setup stage, per output row r (ascending eigenvalue)
@@ -142,6 +143,7 @@ void free_plan_tables(dctplus_plan_t p);
 
 // hier.cu
 constexpr int kHierAutoMin = 2048;  // AUTO picks the hierarchical product from this n on
+constexpr int kTreeAutoMin = 8192;  // the far field's default form: the tree from this n on
 bool hier_shape(int n);
 dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd);
 void free_hier(HierTables* h);
@@ -188,14 +190,19 @@ dctplus_status launch_small_simt_f32(dctplus_plan_t p, const float* x, int64_t l
 // Far-field outputs of the DCT-II kernel for the hierarchical Cauchy product
 // (hier.cu): with s in shared memory the kernel also forms, per signal, the
 // leaf moments of the far field (P2M) and the values of the dense rows.
-constexpr int kFarR = 12;     // Chebyshev degree (moments per leaf)
-constexpr int kFarTqLd = 24;  // row pitch of the P2M table (conflict-free fragment loads)
+constexpr int kFarR = 12;     // Chebyshev degree (moments per box)
+constexpr int kFarTqLd = 24;  // row pitch of the P2M and M2M tables (conflict-free fragment loads)
+constexpr int kFarMaxLev = 8; // tree levels (leaf level included), nleaf <= 256
 struct DctFar {
     const float* zf;      // n: z_j, 0 where deflated
     const float* tq_hi;   // 64 x kFarTqLd: S_a(u_jj) at the 64 source positions of a leaf
     const float* tq_lo;   // (a < 12; other columns 0), TF32 hi and remainder
-    float* mc;            // leaf moments: mc[b * ldm + leaf * 12 + a] = sum_jj S_a(u_jj) z_j s_j
-    int64_t ldm;
+    float* mc;            // moments of the tree boxes: leaf level (P2M) mc[b * ldm + leaf * 12 + a]
+    int64_t ldm;          //   = sum_jj S_a(u_jj) z_j s_j, level l at lev_off[l] (M2M)
+    const float* tm_hi;   // M2M re-expansion [24][kFarTqLd]: row k = child * 12 + b, column a
+    const float* tm_lo;   //   holds S_a^parent(child's node b), TF32 hi and remainder
+    int nlev;             // levels formed here (1: leaf moments only)
+    int lev_off[kFarMaxLev];
     const float* out_g;   // nout x n: for the rows whose eigenvalue mu_o lies outside [0, 4],
     int nout;             // g_oj = -a_o / (mu_o - lambda_j) (0 where z_j = 0)
     float* dv;            // their values dv[b * ldd + o] = sum_j g_oj z_j s_j (slots

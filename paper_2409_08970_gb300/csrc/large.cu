@@ -312,19 +312,6 @@ static dctplus_status launch_r8(int n, const float* x, int64_t ldx, float* s_out
 
 // ------------------------------------------------- DCT-II + far-field moments
 
-// D += A B for one m16n8k8 TF32 tile (mma.sync). The leaf-moment contraction
-// below is a few multiply-adds per sample inside a CUDA-core kernel, too small
-// to pay for a tcgen05 pipeline; the warp-level instruction keeps it off the
-// FMA pipe that the FFT saturates.
-__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], const uint32_t (&a)[4],
-                                                 const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-        "{%8, %9}, {%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // shared-memory index of coefficient j in the P2M staging buffer: 4 pad
 // floats per leaf of 64 keep the fragment loads conflict-free
 __device__ __forceinline__ int far_phys(int j) { return j + 4 * (j >> 6); }
@@ -360,7 +347,8 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
     float* wall = reinterpret_cast<float*>(dsm + spc * BUF);  // [spc][WB]: w = z s
     float* wb = wall + slot * WB;
     float* tqs = wall + spc * WB;                              // [2][64][kFarTqLd]: hi, lo
-    float* red = tqs + 2 * 64 * kFarTqLd;                      // [spc][kWps][2]
+    float* tms = tqs + 2 * 64 * kFarTqLd;                      // [2][24][kFarTqLd]: hi, lo
+    float* red = tms + 2 * 24 * kFarTqLd;                      // [spc][kWps][2]
     const float2* __restrict__ tw_split = tw + M;
     const float2* __restrict__ tw_post = tw + 2 * M + 1;
     const float2* __restrict__ twp = tw + 3 * M + 2;
@@ -368,6 +356,11 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
         tqs[e] = F.tq_hi[e];
         tqs[64 * kFarTqLd + e] = F.tq_lo[e];
     }
+    if (F.nlev > 1)
+        for (int e = threadIdx.x; e < 24 * kFarTqLd; e += blockDim.x) {
+            tms[e] = F.tm_hi[e];
+            tms[24 * kFarTqLd + e] = F.tm_lo[e];
+        }
     const int ntile = (spc * NLEAF + 15) / 16;  // P2M row tiles of this CTA
     for (int64_t base = (int64_t)blockIdx.x * spc; base < batch; base += (int64_t)gridDim.x * spc) {
         const int64_t sig = base + slot;
@@ -438,12 +431,6 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                 const int k0 = 8 * ks + tg;
                 const float af[4] = {wrow[0] ? wrow[0][k0] : 0.f, wrow[1] ? wrow[1][k0] : 0.f,
                                      wrow[0] ? wrow[0][k0 + 4] : 0.f, wrow[1] ? wrow[1][k0 + 4] : 0.f};
-                uint32_t ahi[4], alo[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    ahi[e] = __float_as_uint(af[e]) & ~0x1FFFu;
-                    alo[e] = ptx::cvt_rna_tf32(af[e] - __uint_as_float(ahi[e]));
-                }
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
                     const int c = 8 * nt + g;
@@ -451,10 +438,8 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                                              __float_as_uint(tqs[(k0 + 4) * kFarTqLd + c])};
                     const uint32_t blo[2] = {__float_as_uint(tqs[64 * kFarTqLd + k0 * kFarTqLd + c]),
                                              __float_as_uint(tqs[64 * kFarTqLd + (k0 + 4) * kFarTqLd + c])};
-                    float d[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_m16n8k8_tf32(d, ahi, blo);
-                    mma_m16n8k8_tf32(d, alo, bhi);
-                    mma_m16n8k8_tf32(d, ahi, bhi);
+                    float d[4];
+                    ptx::mma_split_tf32(d, af, bhi, blo);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) acc[nt][e] += d[e];
                 }
@@ -465,11 +450,65 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                 for (int e = 0; e < 4; ++e) {
                     const int h = e >> 1, a = 8 * nt + 2 * tg + (e & 1);
                     if (a >= kFarR || rsig[h] < 0) continue;
-                    const int64_t o = rsig[h] * F.ldm + rleaf[h] * kFarR + a;
-                    F.mc[o] = acc[nt][e];
+                    F.mc[rsig[h] * F.ldm + rleaf[h] * kFarR + a] = acc[nt][e];
+                    // the leaf moments stay on chip for M2M (the FFT buffer is free now)
+                    if (F.nlev > 1)
+                        reinterpret_cast<float*>(dsm + (rsig[h] - base) * BUF)[rleaf[h] * kFarR + a] = acc[nt][e];
                 }
         }
-        __syncthreads();  // the dense rows' partial sums are in red
+        __syncthreads();  // the dense rows' partial sums are in red, the leaf moments on chip
+        // M2M: level l moments of parent p = E_0 M(left child) + E_1 M(right child), one
+        // m16n8k8 row tile of (signal slot, parent) rows per warp, K = 24 (both children)
+        for (int l = 1; l < F.nlev; ++l) {
+            const int nb = NLEAF >> l;
+            if (warp < (spc * nb + 15) / 16) {
+                const int g = lane >> 2, tg = lane & 3;
+                const float* arow[2];
+                float* orow[2];
+                int64_t osig[2];
+                int ocol[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = 16 * warp + g + 8 * h;
+                    const int sl_ = r / nb, p = r % nb;
+                    const bool ok = sl_ < spc && base + sl_ < batch;
+                    float* mom = reinterpret_cast<float*>(dsm + sl_ * BUF);
+                    ocol[h] = F.lev_off[l] + p * kFarR;
+                    arow[h] = ok ? mom + F.lev_off[l - 1] + 2 * p * kFarR : nullptr;
+                    orow[h] = ok ? mom + ocol[h] : nullptr;
+                    osig[h] = ok ? base + sl_ : -1;
+                }
+                float acc[2][4] = {};
+#pragma unroll
+                for (int ks = 0; ks < 3; ++ks) {
+                    const int k0 = 8 * ks + tg;
+                    const float af[4] = {arow[0] ? arow[0][k0] : 0.f, arow[1] ? arow[1][k0] : 0.f,
+                                         arow[0] ? arow[0][k0 + 4] : 0.f, arow[1] ? arow[1][k0 + 4] : 0.f};
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        const int c = 8 * nt + g;
+                        const uint32_t bhi[2] = {__float_as_uint(tms[k0 * kFarTqLd + c]),
+                                                 __float_as_uint(tms[(k0 + 4) * kFarTqLd + c])};
+                        const uint32_t blo[2] = {__float_as_uint(tms[24 * kFarTqLd + k0 * kFarTqLd + c]),
+                                                 __float_as_uint(tms[24 * kFarTqLd + (k0 + 4) * kFarTqLd + c])};
+                        float d[4];
+                        ptx::mma_split_tf32(d, af, bhi, blo);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[nt][e] += d[e];
+                    }
+                }
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int h = e >> 1, a = 8 * nt + 2 * tg + (e & 1);
+                        if (a >= kFarR || osig[h] < 0) continue;
+                        orow[h][a] = acc[nt][e];
+                        F.mc[osig[h] * F.ldm + ocol[h] + a] = acc[nt][e];
+                    }
+            }
+            __syncthreads();
+        }
         if (live) {  // the 32 dense-row slots: values, then zeros
             for (int o = t; o < 32; o += TPS) {
                 float val = 0.f;
@@ -495,7 +534,7 @@ static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_ou
         grid = std::min<int64_t>(grid, (batch + spc - 1) / spc);
     }
     smem = (size_t)spc * sizeof(float2) * (M + M / 8) +
-           sizeof(float) * ((size_t)spc * (2 * M + M / 8) + 2 * 64 * kFarTqLd + spc * kWps * 2);
+           sizeof(float) * ((size_t)spc * (2 * M + M / 8) + 2 * 64 * kFarTqLd + 2 * 24 * kFarTqLd + spc * kWps * 2);
     static bool attr[64] = {};
     if (!attr[dev & 63]) {
         DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_far<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -512,7 +551,8 @@ static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_ou
 
 dctplus_status launch_dct_far(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds, int64_t batch, const DctFar& far, cudaStream_t st) {
     const int n = p->n;
-    if (!p->d_twiddle || batch > INT32_MAX || far.nout > 2) return DCTPLUS_ERR_UNSUPPORTED;
+    if (!p->d_twiddle || batch > INT32_MAX || far.nout > 2 || far.nlev < 1 || far.nlev > kFarMaxLev)
+        return DCTPLUS_ERR_UNSUPPORTED;
     if (batch <= 0) return DCTPLUS_OK;
     const int vec = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
     const float2* tw = reinterpret_cast<const float2*>(p->d_twiddle);

@@ -431,6 +431,7 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
             (m == DCTPLUS_CAUCHY_HIER && !hier_shape(n)))
             return DCTPLUS_ERR_UNSUPPORTED;
         p->cauchy_mode = m;
+        if (m == DCTPLUS_CAUCHY_HIER && p->far_field == 0) p->far_field = n >= kTreeAutoMin ? 2 : 1;
     }
     const bool want_xt = p->cauchy_mode == DCTPLUS_CAUCHY_DENSE_GFT;
     // W split is also the operand that builds X^T for the comparator beyond the FP64 table size

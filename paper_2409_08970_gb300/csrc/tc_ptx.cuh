@@ -218,6 +218,21 @@ __device__ __forceinline__ bool named_bar_and(int id, int nthreads, bool pred) {
     return r != 0;
 }
 
+// D += A B for one m16n8k8 TF32 tile (warp-level mma.sync). Used for the far
+// field's block contractions: 12 x 12 blocks for groups of 16 signals, too
+// small for the 128-row tcgen05 tiles. Fragments (g = lane / 4, t = lane % 4):
+// A rows g, g + 8 and columns t, t + 4 (a0 = (g, t), a1 = (g + 8, t),
+// a2 = (g, t + 4), a3 = (g + 8, t + 4)); B rows (k) t, t + 4 of column g;
+// D rows g, g + 8 and columns 2t, 2t + 1 (d0, d1 row g; d2, d3 row g + 8).
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], const uint32_t (&a)[4],
+                                                 const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+        "{%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 // Shared-memory matrix descriptor, K-major operand in the 128-byte swizzled
 // canonical layout: rows of 128 bytes, 8-row groups 1024 bytes apart (SBO),
 // tile base 1024-byte aligned. Fields: start address >> 4 (bits 0-13), leading
@@ -251,6 +266,23 @@ __device__ __forceinline__ float tf32_round(float v) {
     uint32_t u = __float_as_uint(v);
     u = (u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu;
     return __uint_as_float(u);
+}
+
+// One split-TF32 m16n8k8 step with fresh accumulation: d = A_hi B_lo + A_lo B_hi +
+// A_hi B_hi (the small products first), A given as FP32 values and split here
+// (hi = truncated, lo = rounded remainder), B as TF32 hi and lo fragments.
+__device__ __forceinline__ void mma_split_tf32(float (&d)[4], const float (&af)[4],
+                                               const uint32_t (&bhi)[2], const uint32_t (&blo)[2]) {
+    uint32_t ahi[4], alo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        ahi[e] = __float_as_uint(af[e]) & ~0x1FFFu;
+        alo[e] = cvt_rna_tf32(af[e] - __uint_as_float(ahi[e]));
+    }
+    d[0] = d[1] = d[2] = d[3] = 0.f;
+    mma_m16n8k8_tf32(d, ahi, blo);
+    mma_m16n8k8_tf32(d, alo, bhi);
+    mma_m16n8k8_tf32(d, ahi, bhi);
 }
 
 }  // namespace ptx

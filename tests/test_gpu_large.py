@@ -85,20 +85,44 @@ def test_dense_gft_baseline_matches_oracle(pkg, n):
     plan.close()
 
 
+@pytest.mark.parametrize("far_field", [1, 2])
 @pytest.mark.parametrize("n", [256, 512, 1024, 4096])
-def test_hierarchical_mode_matches_oracle(pkg, n):
-    batch = 150
+def test_hierarchical_mode_matches_oracle(pkg, n, far_field):
+    """Both far-field forms (leaf level, multipole tree) against the Cauchy formula; the
+    batch is ragged for the 128-signal GEMM tiles and the 256-signal tree CTAs."""
+    batch = 150 if n < 4096 else 300
     cases = [(random_unit_v(n), -0.3), (random_unit_v(n), 2.0), (self_loop_v(n, 0), 1.0),
              (edge_update_v(n, n // 2 - 1, n // 2), -0.5), (edge_update_v(n, 5, 6), 3.0)]
     for v, rho in cases:
         x = normal_signals(batch, n, seed=n + 1)
         ref = cauchy.transform(cauchy.make_plan(n, v, rho), x)
-        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_HIER)
-        assert plan.cauchy_mode == pkg.CAUCHY_HIER
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_HIER, far_field=far_field)
+        assert plan.cauchy_mode == pkg.CAUCHY_HIER and plan.far_field == far_field
         err = relerr(run32(plan, x), ref)
-        assert err.max() < F32_TOL, (n, rho, err.max())
+        assert err.max() < F32_TOL, (n, rho, far_field, err.max())
         plan.close()
     assert pkg.dctplus_sync_check(0) == 0
+
+
+def test_far_field_forms_agree_and_default(pkg):
+    """The two far-field forms give the same transform; the default is the tree from n = 8192."""
+    n, batch = 2048, 200
+    v = random_unit_v(n)
+    x = normal_signals(batch, n, seed=5)
+    a = pkg.Plan(n, v, 2.0, cauchy_mode=pkg.CAUCHY_HIER, far_field=1)
+    b = pkg.Plan(n, v, 2.0, cauchy_mode=pkg.CAUCHY_HIER, far_field=2)
+    assert relerr(run32(a, x), run32(b, x)).max() < 2 * F32_TOL
+    a.close()
+    b.close()
+    for m, want in [(4096, 1), (8192, 2), (16384, 2)]:
+        p = pkg.Plan(m, self_loop_v(m, 0), 1.0, cauchy_mode=pkg.CAUCHY_HIER)
+        assert p.far_field == want, m
+        p.close()
+    d = pkg.Plan(1024, v[:1024] / np.linalg.norm(v[:1024]), 1.0, cauchy_mode=pkg.CAUCHY_DENSE)
+    assert d.far_field == 0
+    d.close()
+    with pytest.raises(pkg.DctPlusError):
+        pkg.Plan(1024, self_loop_v(1024, 0), 1.0, cauchy_mode=pkg.CAUCHY_HIER, far_field=3)
 
 
 def test_hierarchical_n16384_sampled(pkg):
@@ -116,6 +140,24 @@ def test_hierarchical_n16384_sampled(pkg):
         assert err.max() < F32_TOL, err.max()
         pr = np.abs(np.linalg.norm(y, axis=1) / np.linalg.norm(x, axis=1) - 1)
         assert pr.max() < 2e-6
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
+
+
+@pytest.mark.parametrize("far_field", [1, 2])
+def test_hierarchical_full_batch_sampled(pkg, far_field):
+    """n = 1024, batch 4096 in the hierarchical mode: the launch configuration the benchmark
+    times, checked on 128 sampled signals against the Cauchy formula."""
+    n, batch = 1024, 4096
+    v = random_unit_v(n)
+    x = normal_signals(batch, n, seed=0)
+    for rho in (-0.3, 2.0):
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_HIER, far_field=far_field)
+        y = run32(plan, x)
+        rng = np.random.default_rng(3)
+        sig = np.sort(rng.choice(batch, 128, replace=False))
+        ref = cauchy.transform(cauchy.make_plan(n, v, rho), x[sig])
+        assert relerr(y[sig], ref).max() < F32_TOL
         plan.close()
     assert pkg.dctplus_sync_check(0) == 0
 
