@@ -357,11 +357,12 @@ def run_ours(args):
         peaks = (hbm_peak, bf16_peak, peak_src)
         errs = not args.no_cpu
         extra["fp64_n64"] = bench_fp64_n64(pkg, torch, dev, stream, args, flush, peaks)
-        extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 1024, 4096, [H, D, G], errs)
+        HL, HT = (H, 1), (H, 2)
+        extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 1024, 4096, [HL, HT, D, G], errs)
         if not args.quick:
-            extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 256, 4096, [H, D, G], errs)
-            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 4096, 4096, [H, D, G], errs)
-            extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 16384, 512, [H], errs)
+            extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 256, 4096, [HL, HT, D, G], errs)
+            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 4096, 4096, [HL, HT, D, G], errs)
+            extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 16384, 512, [HL, HT], errs)
         extra["pruned_n512"] = bench_pruned(pkg, torch, dev, stream, args, flush, peaks)
         extra["backward_n1024"] = bench_backward(pkg, torch, dev, stream, args, flush, peaks)
         extra["dense_gft_cublas_fp32"] = bench_dense_gft(pkg, torch, dev, stream, args, flush, wl,
@@ -420,9 +421,10 @@ def bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, er
     out = {"workload": f"n={n}, batch {batch}, x~N(0,1), dense unit v (seed 1), rho in {{-0.3, 2.0}}; "
                        "one step = both plans over the batch"}
     for mode in modes:
+        mode, far = mode if isinstance(mode, tuple) else (mode, 0)
         try:
             t0 = time.perf_counter()
-            plans = [pkg.Plan(n, v, rho, cauchy_mode=mode) for rho in rhos]
+            plans = [pkg.Plan(n, v, rho, cauchy_mode=mode, far_field=far) for rho in rhos]
             plan_ms = (time.perf_counter() - t0) * 1e3 / len(rhos)
         except pkg.DctPlusError:
             continue
@@ -453,9 +455,17 @@ def bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, er
                                                     "normwise_rel_max")}
             entry["fp32_err_vs_fp64_oracle"]["snr_db_mean"] = float(np.mean([e["snr_db_mean"] for e in errs]))
             entry["fp32_err_vs_fp64_oracle"]["sample"] = errs[0]["sample"] + " per plan"
-        out[MODE_NAMES.get(plans[0].cauchy_mode, str(mode))] = entry
+        name = MODE_NAMES.get(plans[0].cauchy_mode, str(mode))
+        if plans[0].cauchy_mode == pkg.CAUCHY_HIER:
+            name += {1: "_leaf_level", 2: "_tree"}.get(plans[0].far_field, "")
+        out[name] = entry
         for p in plans:
             p.close()
+    if n > 64:  # what the autotuner measures and would pick for this n and batch (rho = 2.0)
+        t = pkg.dctplus_autotune(n, v, 2.0, batch, None, sh)
+        out["autotune"] = {"choice": {1: "dense", 2: "hierarchical", 3: "cuda_core"}.get(t["cauchy_mode"]),
+                           "far_field": t["far_field"], "ms_per_call": t["ms"],
+                           "note": "per call of one plan over the batch, not L2-flushed"}
     return out
 
 
@@ -766,8 +776,9 @@ def run_only(args):
         flush_buf.fill_(1.0)
 
     D, H, G = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT
-    large = {"n256": (256, 4096, [H, D, G]), "n1024": (1024, 4096, [H, D, G]),
-             "n4096": (4096, 4096, [H, D, G]), "n16384": (16384, 512, [H])}
+    HL, HT = (H, 1), (H, 2)
+    large = {"n256": (256, 4096, [HL, HT, D, G]), "n1024": (1024, 4096, [HL, HT, D, G]),
+             "n4096": (4096, 4096, [HL, HT, D, G]), "n16384": (16384, 512, [HL, HT])}
     if args.only in large:
         n, batch, modes = large[args.only]
         out = bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, not args.no_cpu)

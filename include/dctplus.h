@@ -96,6 +96,12 @@ typedef struct {
                              2 (12 n / 64)^2 floats of tables), 2 = multipole tree (M2M, M2L,
                              L2L over the angle boxes: O(n log n) work, O(n) tables) */
     int device;           /* CUDA device ordinal; -1 = current device */
+    int64_t batch_hint;   /* expected batch, for the autotune cache lookup (0 = 4096) */
+    const char* tune_cache; /* autotune cache file read when cauchy_mode is AUTO (see
+                             dctplus_autotune); NULL = the DCTPLUS_TUNE_CACHE environment
+                             variable, if set. With no matching entry AUTO takes its fixed
+                             rule: dense for 128 <= n < 1024 (n % 128 == 0), hierarchical from
+                             1024 (powers of two), the CUDA-core product otherwise. */
 } dctplus_opts;
 
 /* ------------------------------------------------------------------ plans */
@@ -299,6 +305,38 @@ dctplus_status dctplus_execute_group_host(dctplus_group_t group, const float* x_
 /* Synchronises `stream`, then reads and clears the device error word.
  * Returns DCTPLUS_OK, DCTPLUS_ERR_DEVICE_CHECK or DCTPLUS_ERR_TIMEOUT. */
 dctplus_status dctplus_sync_check(dctplus_stream_t stream);
+
+/* ------------------------------------------------------------ autotuning */
+
+/* Measures the FP32 Cauchy evaluations that apply at length n (dense tensor-core
+ * product, hierarchical with the leaf-level far field, hierarchical with the
+ * tree, CUDA-core product) for the update (v_host, rho) and `batch` signals
+ * (generated on the device, a hash of the element index in [-1, 1)) on this
+ * device: three warm-up calls, then five timed calls each (CUDA events on
+ * `stream`). Every candidate's output on 16 sampled signals must agree with the
+ * CUDA-core product's to 4e-6 normwise, else it is not chosen. Writes the
+ * fastest correct choice to *cauchy_mode and *far_field, the per-call ms of each
+ * candidate to candidate_ms[4] (dense, hierarchical leaf level, hierarchical
+ * tree, CUDA cores; -1 where not applicable or not correct; may be NULL), and,
+ * with cache_path non-NULL, records the choice there under (this device's name,
+ * n, batch rounded up to a power of two), replacing an entry with that key.
+ * A tuning call: it allocates (3 batch n floats) and synchronises; 64 < n <= 16384,
+ * batch n <= 2^28. The paper has no counterpart. Errors: INVALID_ARG,
+ * UNSUPPORTED (no candidate ran), NO_DEVICE, CUDA. */
+dctplus_status dctplus_autotune(int n, const double* v_host, double rho, int64_t batch,
+                                const char* cache_path, dctplus_stream_t stream, int* cauchy_mode,
+                                int* far_field, double* candidate_ms);
+
+/* Host-only access to an autotune cache file (no GPU needed). Lookup writes the
+ * entry for (device_name, n, batch rounded up to a power of two) and returns OK,
+ * or returns UNSUPPORTED when there is none (or the file is missing). Record
+ * adds or replaces that entry (candidate_ms[4] may be NULL); the file is
+ * rewritten through a temporary file and renamed. */
+dctplus_status dctplus_tune_lookup(const char* cache_path, const char* device_name, int n,
+                                   int64_t batch, int* cauchy_mode, int* far_field);
+dctplus_status dctplus_tune_record(const char* cache_path, const char* device_name, int n,
+                                   int64_t batch, int cauchy_mode, int far_field, double ms,
+                                   const double* candidate_ms);
 
 /* Number of kernels this library has launched in this process (all devices). */
 int64_t dctplus_launch_count(void);

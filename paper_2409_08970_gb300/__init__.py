@@ -28,7 +28,7 @@ __all__ = [
     "dctplus_backward", "dctplus_group_create", "DctPlusFunction", "dct_plus", "dctplus_group_destroy",
     "dctplus_execute_group", "dctplus_execute_group_host", "dctplus_sync_check",
     "dctplus_launch_count", "dctplus_status_string", "dctplus_trace_begin", "dctplus_trace_end",
-    "library_path",
+    "dctplus_autotune", "dctplus_tune_lookup", "dctplus_tune_record", "library_path",
 ]
 
 
@@ -145,6 +145,48 @@ def dctplus_sync_check(stream: int = 0) -> int:
     return int(_lib.load().dctplus_sync_check(stream))
 
 
+CANDIDATES = ("dense", "hier_leaf", "hier_tree", "simt")
+
+
+def dctplus_autotune(n: int, v, rho: float, batch: int, cache_path: str | None = None,
+                     stream: int = 0) -> dict:
+    """Times the Cauchy evaluations that apply at length n on this device and returns the
+    fastest correct one: {"cauchy_mode", "far_field", "ms": {candidate: ms per call}}; with
+    cache_path the choice is recorded there (see include/dctplus.h)."""
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    if v.shape != (n,):
+        raise ValueError("v must have shape (n,)")
+    mode, far = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_double * 4)()
+    st = _lib.load().dctplus_autotune(int(n), v.ctypes.data, float(rho), int(batch),
+                                      cache_path.encode() if cache_path else None, stream,
+                                      ctypes.byref(mode), ctypes.byref(far), ms)
+    check(st, "dctplus_autotune")
+    return {"cauchy_mode": mode.value, "far_field": far.value,
+            "ms": {k: ms[i] for i, k in enumerate(CANDIDATES)}}
+
+
+def dctplus_tune_lookup(cache_path: str, device_name: str, n: int, batch: int):
+    """(cauchy_mode, far_field) recorded for (device, n, batch bucket), or None."""
+    mode, far = ctypes.c_int(), ctypes.c_int()
+    st = _lib.load().dctplus_tune_lookup(cache_path.encode(), device_name.encode(), int(n), int(batch),
+                                         ctypes.byref(mode), ctypes.byref(far))
+    if st == _lib.ERR_UNSUPPORTED:
+        return None
+    check(st, "dctplus_tune_lookup")
+    return mode.value, far.value
+
+
+def dctplus_tune_record(cache_path: str, device_name: str, n: int, batch: int, cauchy_mode: int,
+                        far_field: int, ms: float, candidate_ms=None) -> None:
+    cand = None
+    if candidate_ms is not None:
+        cand = (ctypes.c_double * 4)(*[float(c) for c in candidate_ms])
+    check(_lib.load().dctplus_tune_record(cache_path.encode(), device_name.encode(), int(n), int(batch),
+                                          int(cauchy_mode), int(far_field), float(ms), cand),
+          "dctplus_tune_record")
+
+
 def dctplus_trace_begin(stream: int) -> None:
     check(_lib.load().dctplus_trace_begin(stream), "dctplus_trace_begin")
 
@@ -167,10 +209,12 @@ class Plan:
     """A Fast DCT+ plan: the GFT of L~ + rho v v^T for signals of length n."""
 
     def __init__(self, n: int, v, rho: float, cauchy_mode: int = CAUCHY_AUTO,
-                 max_secular_iter: int = 0, far_field: int = 0, device: int = -1):
+                 max_secular_iter: int = 0, far_field: int = 0, device: int = -1,
+                 batch_hint: int = 0, tune_cache: str | None = None):
         self.n = int(n)
         self.rho = float(rho)
-        opts = Opts(cauchy_mode, max_secular_iter, far_field, device)
+        opts = Opts(cauchy_mode, max_secular_iter, far_field, device, int(batch_hint),
+                    tune_cache.encode() if tune_cache else None)
         self.handle = dctplus_plan(self.n, v, self.rho, opts)
 
     @property

@@ -40,7 +40,8 @@ EXPORTS = (
     "dctplus_execute_noalloc", "dctplus_execute_pruned", "dctplus_backward",
     "dctplus_group_create", "dctplus_group_destroy", "dctplus_execute_group",
     "dctplus_execute_group_host", "dctplus_sync_check", "dctplus_launch_count",
-    "dctplus_status_string", "dctplus_trace_begin", "dctplus_trace_end",
+    "dctplus_status_string", "dctplus_trace_begin", "dctplus_trace_end", "dctplus_autotune",
+    "dctplus_tune_lookup", "dctplus_tune_record",
 )
 
 
@@ -53,7 +54,8 @@ class DctPlusError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("cauchy_mode", ctypes.c_int), ("max_secular_iter", ctypes.c_int),
-                ("far_field", ctypes.c_int), ("device", ctypes.c_int)]
+                ("far_field", ctypes.c_int), ("device", ctypes.c_int),
+                ("batch_hint", ctypes.c_int64), ("tune_cache", ctypes.c_char_p)]
 
 
 _lib = None
@@ -88,6 +90,9 @@ def load():
         "dctplus_launch_count": (i64, []),
         "dctplus_status_string": (ctypes.c_char_p, [c_int]),
         "dctplus_trace_begin": (c_int, [vp]),
+        "dctplus_autotune": (c_int, [c_int, vp, c_double, i64, ctypes.c_char_p, vp, vp, vp, vp]),
+        "dctplus_tune_lookup": (c_int, [ctypes.c_char_p, ctypes.c_char_p, c_int, i64, vp, vp]),
+        "dctplus_tune_record": (c_int, [ctypes.c_char_p, ctypes.c_char_p, c_int, i64, c_int, c_int, c_double, vp]),
         "dctplus_trace_end": (c_int, [vp, vp, vp, vp, vp, c_int]),
     }
     for name, (res, args) in sig.items():

@@ -137,12 +137,16 @@ struct TcSegHost {
 bool small_tc_capable(dctplus_plan_t p);
 dctplus_status launch_tc_segments(const std::vector<TcSegHost>& segs, cudaStream_t s, int dev);
 
+// autotune.cu: the cache entry for (device, n, batch bucket), if any
+int64_t tune_bucket(int64_t batch);
+bool tune_lookup(const char* path, const char* device, int n, int64_t batch, int* mode, int* far);
+
 // plan.cu
 dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o);
 void free_plan_tables(dctplus_plan_t p);
 
 // hier.cu
-constexpr int kHierAutoMin = 2048;  // AUTO picks the hierarchical product from this n on
+constexpr int kHierAutoMin = 1024;  // AUTO picks the hierarchical product from this n on
 constexpr int kTreeAutoMin = 8192;  // the far field's default form: the tree from this n on
 bool hier_shape(int n);
 dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd);

@@ -9,6 +9,7 @@
 // from a table of sin(pi m / 2n), m = 0..n, with the first argument reflected
 // to m = min(j+o, 2n-j-o). No gap is the difference of two rounded eigenvalues.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -422,8 +423,21 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
     if (n > kSmallMax) {
         int m = p->cauchy_mode;
         if (m == DCTPLUS_CAUCHY_AUTO) {
-            if (hier_shape(n) && n >= kHierAutoMin) m = DCTPLUS_CAUCHY_HIER;
-            else m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
+            // a measured choice from the autotune cache, if one applies
+            const char* cache = o.tune_cache ? o.tune_cache : std::getenv("DCTPLUS_TUNE_CACHE");
+            int tm = -1, tf = 0;
+            cudaDeviceProp prop;
+            if (cache && *cache && cudaGetDeviceProperties(&prop, p->device) == cudaSuccess &&
+                tune_lookup(cache, prop.name, n, o.batch_hint > 0 ? o.batch_hint : 4096, &tm, &tf) &&
+                ((tm == DCTPLUS_CAUCHY_DENSE && gemm_shape) || (tm == DCTPLUS_CAUCHY_HIER && hier_shape(n) && tf > 0) ||
+                 tm == DCTPLUS_CAUCHY_SIMT)) {
+                m = tm;
+                if (m == DCTPLUS_CAUCHY_HIER && p->far_field == 0) p->far_field = tf;
+            } else if (hier_shape(n) && n >= kHierAutoMin) {
+                m = DCTPLUS_CAUCHY_HIER;
+            } else {
+                m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
+            }
         }
         if ((m == DCTPLUS_CAUCHY_NFST && n > kF64Max) ||
             (m == DCTPLUS_CAUCHY_DENSE && !gemm_shape) ||

@@ -57,7 +57,7 @@ def test_dense_and_cuda_core_modes_agree(pkg):
 
 
 def test_auto_mode_choice(pkg):
-    for n, want in [(128, pkg.CAUCHY_DENSE), (1024, pkg.CAUCHY_DENSE), (4096, pkg.CAUCHY_HIER),
+    for n, want in [(128, pkg.CAUCHY_DENSE), (512, pkg.CAUCHY_DENSE), (1024, pkg.CAUCHY_HIER), (4096, pkg.CAUCHY_HIER),
                     (16384, pkg.CAUCHY_HIER)]:
         p = pkg.Plan(n, self_loop_v(n, 0), 1.0)
         assert p.cauchy_mode == want, n
@@ -168,7 +168,7 @@ def test_dense_mode_full_batch_sampled(pkg):
     v = random_unit_v(n)
     x = normal_signals(batch, n, seed=0)
     for rho in (-0.3, 2.0):
-        plan = pkg.Plan(n, v, rho)
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_DENSE)
         y = run32(plan, x)
         rng = np.random.default_rng(2)
         sig = np.sort(rng.choice(batch, 128, replace=False))

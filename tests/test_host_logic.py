@@ -62,3 +62,36 @@ def test_autograd_value_keys_are_memoised_per_tensor_version():
     w = v.clone()
     assert pkg._value_key(w, to_host) == k3 and len(calls) == 3  # equal values, other tensor
     assert pkg._value_key(1.5, float) == 1.5     # plain numbers are their own key
+
+
+def test_autotune_cache_record_and_lookup(tmp_path):
+    """The autotune cache (host-only entry points): record, lookup by (device, n, batch
+    bucket), replacement of an entry with the same key, other keys untouched, a missing file
+    or key reported as no entry, and lines that do not parse skipped."""
+    import json
+
+    import paper_2409_08970_gb300 as pkg
+    path = str(tmp_path / "tune.json")
+    dev = "NVIDIA GB300"
+    assert pkg.dctplus_tune_lookup(path, dev, 1024, 4096) is None          # no file yet
+    pkg.dctplus_tune_record(path, dev, 1024, 4096, pkg.CAUCHY_HIER, 1, 0.061, [0.07, 0.061, 0.09, 0.5])
+    pkg.dctplus_tune_record(path, dev, 4096, 4000, pkg.CAUCHY_HIER, 2, 0.2)
+    pkg.dctplus_tune_record(path, "other device", 1024, 4096, pkg.CAUCHY_DENSE, 0, 0.05)
+    assert pkg.dctplus_tune_lookup(path, dev, 1024, 4096) == (pkg.CAUCHY_HIER, 1)
+    assert pkg.dctplus_tune_lookup(path, dev, 1024, 3000) == (pkg.CAUCHY_HIER, 1)   # same bucket 4096
+    assert pkg.dctplus_tune_lookup(path, dev, 1024, 5000) is None                    # bucket 8192
+    assert pkg.dctplus_tune_lookup(path, dev, 4096, 4096) == (pkg.CAUCHY_HIER, 2)
+    assert pkg.dctplus_tune_lookup(path, "other device", 1024, 4096) == (pkg.CAUCHY_DENSE, 0)
+    pkg.dctplus_tune_record(path, dev, 1024, 4096, pkg.CAUCHY_DENSE, 0, 0.05)     # replace
+    assert pkg.dctplus_tune_lookup(path, dev, 1024, 4096) == (pkg.CAUCHY_DENSE, 0)
+    d = json.load(open(path))                                                   # valid JSON
+    assert len(d["entries"]) == 3
+    e = [x for x in d["entries"] if x["n"] == 4096][0]
+    assert e["batch_bucket"] == 4096 and e["far_field"] == 2 and e["ms_dense"] == -1
+    # a damaged line is skipped, the others still read
+    text = open(path).read().replace('"other device"', '"other device', 1)
+    open(path, "w").write(text)
+    assert pkg.dctplus_tune_lookup(path, dev, 4096, 4096) == (pkg.CAUCHY_HIER, 2)
+    assert pkg.dctplus_tune_lookup(path, "other device", 1024, 4096) is None
+    with pytest.raises(pkg.DctPlusError):
+        pkg.dctplus_tune_record(path, dev, 1024, 4096, 9, 0, 0.1)                 # bad mode
