@@ -50,6 +50,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 # FP64 on the CUDA cores (nominal, no measured figure): 1.25 TFLOP/s
 FP64_NOMINAL_TFLOPS = 1.25
 TENSOR_KERNELS = ("k_gemm_tc", "k_small_tc")
+FP64_ALU_KERNELS = ("k_nfst_fast", "k_nfst_route")  # the paper's route: FP64 arithmetic on CUDA cores
 
 
 def trace_kernels(pkg, torch, stream, step, flush, reps=3):
@@ -73,7 +74,8 @@ def trace_kernels(pkg, torch, stream, step, flush, reps=3):
 
 def roofline_of(recs, hbm_peak, bf16_peak, peak_src):
     """Roofline object of the dominant kernel (largest summed time over the step's launches of
-    that kernel): tensor-bound for the tensor-core GEMMs (split-TF32 peak), HBM otherwise."""
+    that kernel): tensor-bound for the tensor-core GEMMs (split-TF32 peak), FP64-ALU bound for
+    the paper's trigonometric route (nominal FP64 rate), HBM otherwise."""
     by = {}
     for r in recs:
         e = by.setdefault(r["kernel"], {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "launches": 0})
@@ -91,6 +93,12 @@ def roofline_of(recs, hbm_peak, bf16_peak, peak_src):
                 "frac": achieved / peak,
                 "peak_source": f"{peak_src} bf16_tflops x {TF32_PER_BF16:.4f} (TF32/BF16 nominal "
                                "1.1/2.25 PFLOP/s): split-TF32 products counted as executed",
+                "algorithmic_flops_per_launch": e["flops"] / e["launches"]}
+    elif name in FP64_ALU_KERNELS:
+        achieved = e["flops"] / e["launches"] / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "peak_source": "nominal FP64 CUDA-core rate (no measured FP64 figure)",
                 "algorithmic_flops_per_launch": e["flops"] / e["launches"]}
     else:
         achieved = e["bytes"] / e["launches"] / (per_launch_ms * 1e-3) / 1e9
@@ -353,15 +361,18 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extra and rank == 0:
-        D, H, G = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT
+        D, H, G, R = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT, pkg.CAUCHY_NFST
         peaks = (hbm_peak, bf16_peak, peak_src)
         errs = not args.no_cpu
         extra["fp64_n64"] = bench_fp64_n64(pkg, torch, dev, stream, args, flush, peaks)
         HL, HT = (H, 1), (H, 2)
-        extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 1024, 4096, [HL, HT, D, G], errs)
+        extra["n1024"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 1024, 4096,
+                                     [HL, HT, D, G, R], errs)
         if not args.quick:
-            extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 256, 4096, [HL, HT, D, G], errs)
-            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 4096, 4096, [HL, HT, D, G], errs)
+            extra["n256"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 256, 4096,
+                                        [HL, HT, D, G, R], errs)
+            extra["n4096"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 4096, 4096,
+                                         [HL, HT, D, G, R], errs)
             extra["n16384"] = bench_large(pkg, torch, dev, stream, args, flush, peaks, 16384, 512, [HL, HT], errs)
         extra["pruned_n512"] = bench_pruned(pkg, torch, dev, stream, args, flush, peaks)
         extra["backward_n1024"] = bench_backward(pkg, torch, dev, stream, args, flush, peaks)
@@ -401,7 +412,8 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-MODE_NAMES = {1: "dense", 2: "hierarchical", 3: "cuda_core", 4: "dense_gft_baseline"}
+MODE_NAMES = {1: "dense", 2: "hierarchical", 3: "cuda_core", 4: "dense_gft_baseline",
+              5: "nfst_route_fp64"}
 
 
 def bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, errors=True):
@@ -775,10 +787,10 @@ def run_only(args):
     def flush():
         flush_buf.fill_(1.0)
 
-    D, H, G = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT
+    D, H, G, R = pkg.CAUCHY_DENSE, pkg.CAUCHY_HIER, pkg.CAUCHY_DENSE_GFT, pkg.CAUCHY_NFST
     HL, HT = (H, 1), (H, 2)
-    large = {"n256": (256, 4096, [HL, HT, D, G]), "n1024": (1024, 4096, [HL, HT, D, G]),
-             "n4096": (4096, 4096, [HL, HT, D, G]), "n16384": (16384, 512, [HL, HT])}
+    large = {"n256": (256, 4096, [HL, HT, D, G, R]), "n1024": (1024, 4096, [HL, HT, D, G, R]),
+             "n4096": (4096, 4096, [HL, HT, D, G, R]), "n16384": (16384, 512, [HL, HT])}
     if args.only in large:
         n, batch, modes = large[args.only]
         out = bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, not args.no_cpu)

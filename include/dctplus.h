@@ -79,12 +79,15 @@ typedef enum {
                                     as W U^T on the tensor cores) */
     DCTPLUS_CAUCHY_NFST = 5       /* the paper's own route (Algorithm 1 steps 3-7): the zero
                                     pole's column kept explicit, a DST-I to the Chebyshev
-                                    coefficients, and the sine series over sin(n theta)
-                                    evaluated directly (Clenshaw) instead of by an NFST; FP64
-                                    inside for both dtypes, n <= 1024, O(n^2) per signal.
-                                    Loses accuracy like eps / |sin(n theta)| when a root sits
-                                    next to a pole. Used by dctplus_execute only; groups,
-                                    pruned and backward calls use their own kernels. */
+                                    coefficients, and the sine series over sin(n theta) at the
+                                    roots. FP64 inside for both dtypes. n a power of two with
+                                    16 <= n <= 8192: O(n log n) per signal (FFT-based DCT-II
+                                    and DST-I, the series by a nonuniform sine transform with
+                                    a 16-point Kaiser-Bessel window on a twice-oversampled
+                                    grid); other n <= 1024: direct sums, O(n^2). Loses
+                                    accuracy like eps / |sin(n theta)| when a root sits next
+                                    to a pole. Used by dctplus_execute only; groups, pruned
+                                    and backward calls use their own kernels. */
 } dctplus_cauchy_mode;
 
 typedef struct {

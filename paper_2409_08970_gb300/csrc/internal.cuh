@@ -40,6 +40,7 @@ unsigned* device_error_word(int device);  // lazily allocated per device
 // backward pass (backward.cu).
 struct HierTables;
 struct BackwardTables;
+struct NfstFastTables;
 
 // Tables consumed by the tensor-core small-n kernel (see small_tc.cu).
 struct SmallTcTables {
@@ -93,6 +94,7 @@ struct dctplus_plan_s {
     int* d_nfst_kind = nullptr;
     void* d_nfst_rows = nullptr;
     double* d_nfst_znd = nullptr;
+    dctplus::NfstFastTables* nfst = nullptr;  // O(n log n) route tables (n a power of two <= 8192)
 
     // staging for dctplus_execute_host
     void* d_stage = nullptr;
@@ -182,7 +184,9 @@ dctplus_status launch_rows_gemm(const float* a, int64_t lda, const float* w, int
 void free_backward(BackwardTables* b);
 
 // nfst.cu
+bool nfst_fast_shape(int n);  // n a power of two, 16 <= n <= 8192: the O(n log n) route applies
 dctplus_status setup_nfst(dctplus_plan_t p);
+void free_nfst(NfstFastTables* t);
 template <typename T>
 dctplus_status launch_nfst(dctplus_plan_t p, const T* x, int64_t ldx, T* y, int64_t ldy, int64_t batch,
                            cudaStream_t st);

@@ -291,6 +291,8 @@ void free_plan_tables(dctplus_plan_t p) {
     p->hier = nullptr;
     free_backward(p->bwd);
     p->bwd = nullptr;
+    free_nfst(p->nfst);
+    p->nfst = nullptr;
 }
 
 dctplus_status setup_small_tc(dctplus_plan_t p);   // small_tc.cu
@@ -439,7 +441,7 @@ dctplus_status build_plan(dctplus_plan_t p, const dctplus_opts& o) {
                 m = gemm_shape ? DCTPLUS_CAUCHY_DENSE : DCTPLUS_CAUCHY_SIMT;
             }
         }
-        if ((m == DCTPLUS_CAUCHY_NFST && n > kF64Max) ||
+        if ((m == DCTPLUS_CAUCHY_NFST && n > kF64Max && !nfst_fast_shape(n)) ||
             (m == DCTPLUS_CAUCHY_DENSE && !gemm_shape) ||
             (m == DCTPLUS_CAUCHY_DENSE_GFT && !gemm_shape) ||
             (m == DCTPLUS_CAUCHY_HIER && !hier_shape(n)))

@@ -1,5 +1,7 @@
 """The paper's trigonometric route on the GPU (cauchy mode DCTPLUS_CAUCHY_NFST) against the
-oracle's version of the same route and the Cauchy-formula oracle."""
+oracle's version of the same route and the Cauchy-formula oracle. Powers of two from 16 to 8192
+run the O(n log n) kernel (FFT-based DCT-II and DST-I, nonuniform sine transform); other
+lengths up to 1024 and n = 8 run the direct-sum kernel."""
 import numpy as np
 import pytest
 import scipy.fft
@@ -28,27 +30,40 @@ def conditioning(op):
     return np.abs(np.sin(op.n * th)).min() if inside.any() else 1.0
 
 
-@pytest.mark.parametrize("n", [8, 16, 64, 100, 256, 1024])
+def check_route(pkg, n, v, rho, signals):
+    op = cauchy.make_plan(n, v, rho)
+    x = normal_signals(signals, n, seed=n)
+    plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_NFST)
+    assert plan.cauchy_mode == pkg.CAUCHY_NFST
+    y = plan.forward(torch.tensor(x, dtype=torch.float64, device="cuda")).cpu().numpy()
+    same = nfst_route.transform(op, x)
+    ref = cauchy.transform(op, x)
+    tol = max(1e-12, 1e-13 * n / conditioning(op))
+    e_same = np.linalg.norm(y - same, axis=1) / np.linalg.norm(same, axis=1)
+    e_ref = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert e_same.max() < tol, (n, rho, e_same.max(), tol)
+    assert e_ref.max() < 2 * tol, (n, rho, e_ref.max(), tol)
+    y32 = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    e32 = np.linalg.norm(y32 - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert e32.max() < max(1e-6, 2 * tol), (n, rho, e32.max())
+    plan.close()
+    return op
+
+
+@pytest.mark.parametrize("n", [8, 16, 64, 100, 256, 1024, 2048])
 def test_route_matches_oracles(pkg, n):
     cases = [(random_unit_v(n, seed=7), 0.7), (random_unit_v(n, seed=8), -0.3), (self_loop_v(n, 0), 2.0)]
     if n >= 16:
         cases.append((edge_update_v(n, n // 2 - 1, n // 2), -0.5))
     for v, rho in cases:
-        op = cauchy.make_plan(n, v, rho)
-        x = normal_signals(50, n, seed=n)
-        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_NFST)
-        assert plan.cauchy_mode == pkg.CAUCHY_NFST
-        y = plan.forward(torch.tensor(x, dtype=torch.float64, device="cuda")).cpu().numpy()
-        same = nfst_route.transform(op, x)
-        ref = cauchy.transform(op, x)
-        tol = max(1e-12, 1e-13 * n / conditioning(op))
-        e_same = np.linalg.norm(y - same, axis=1) / np.linalg.norm(same, axis=1)
-        e_ref = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
-        assert e_same.max() < tol, (n, rho, e_same.max(), tol)
-        assert e_ref.max() < 2 * tol, (n, rho, e_ref.max(), tol)
-        y32 = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
-        assert (np.linalg.norm(y32 - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() < 1e-6
-        plan.close()
+        check_route(pkg, n, v, rho, 50)
+    assert pkg.dctplus_sync_check(0) == 0
+
+
+def test_fast_route_at_the_largest_length(pkg):
+    """n = 8192: one CTA of 512 threads per signal, the 147 KB shared buffer, a root beyond 4."""
+    op = check_route(pkg, 8192, random_unit_v(8192, seed=7), 0.7, 6)
+    assert (op.mu >= 4.0).any()
     assert pkg.dctplus_sync_check(0) == 0
 
 
@@ -74,6 +89,8 @@ def test_route_conditioning_next_to_a_pole(pkg):
 
 
 def test_route_size_limit(pkg):
-    with pytest.raises(pkg.DctPlusError) as e:
-        pkg.Plan(2048, self_loop_v(2048, 0), 1.0, cauchy_mode=pkg.CAUCHY_NFST)
-    assert e.value.status == 2
+    """Beyond 1024 only powers of two up to 8192 (the fast kernel's shared buffer) are taken."""
+    for n in (1536, 16384):
+        with pytest.raises(pkg.DctPlusError) as e:
+            pkg.Plan(n, self_loop_v(n, 0), 1.0, cauchy_mode=pkg.CAUCHY_NFST)
+        assert e.value.status == 2

@@ -22,6 +22,10 @@ def test_roofline_of_picks_the_dominant_kernel():
     assert r["achieved"] == pytest.approx(1.0e13 / 25e-6 / 1e12)
     assert r["peak"] == pytest.approx(2000.0 * 1.1 / 2.25)
     assert r["share_of_step"] == pytest.approx(0.05 / 0.07)
+    r3 = bench.roofline_of([{"kernel": "k_nfst_fast", "ms": 2.0, "bytes": 1e8, "flops": 1.0e9}],
+                           6000.0, 2000.0, "measured")
+    assert r3["bound"] == "alu" and r3["peak"] == bench.FP64_NOMINAL_TFLOPS
+    assert r3["achieved"] == pytest.approx(1.0e9 / 2e-3 / 1e12)
     r2 = bench.roofline_of(recs[:1], 6000.0, 2000.0, "measured")
     assert r2["bound"] == "hbm" and r2["unit"] == "GB/s"
     assert r2["achieved"] == pytest.approx(8.0e7 / 10e-6 / 1e9)
