@@ -534,6 +534,8 @@ __device__ __forceinline__ void block12(float (&acc)[kR], const float* T, const 
 // M2L: for every box B of every level, the local expansion
 // v^l[B] = sum over B's interaction list of K(l, B, C) M^l[C].
 // CTA = (box, kTreeThreads signals); the box's slot blocks are staged in shared memory.
+// The output is coefficient-major, vv[(lev_off[l] + B R + a) batch + s], so that a warp's
+// stores (and k_far_down's loads) are contiguous across its signals.
 __global__ void __launch_bounds__(kTreeThreads) k_far_m2l(const FarTree T, const float* __restrict__ mc,
                                                           float* __restrict__ vv, int64_t ldm, int64_t batch) {
     __shared__ __align__(16) float tk[4 * kR * kR];
@@ -549,34 +551,48 @@ __global__ void __launch_bounds__(kTreeThreads) k_far_m2l(const FarTree T, const
     if (s >= batch) return;
     float acc[kR] = {};
     const float* row = mc + s * ldm + T.lev_off[l];
+    float m[4][kR];
 #pragma unroll
-    for (int sl = 0; sl < 4; ++sl) {
-        const int Cb = cbox[sl];
-        if (Cb < 0) continue;  // uniform across the CTA
-        float m[kR];
-        load12(m, row + (int64_t)Cb * kR);
-        block12<false>(acc, tk + sl * kR * kR, m);
-    }
-    store12(vv + s * ldm + T.lev_off[l] + (int64_t)B * kR, acc);
+    for (int sl = 0; sl < 4; ++sl)  // all four loads in flight before the products
+        if (cbox[sl] >= 0) load12(m[sl], row + (int64_t)cbox[sl] * kR);
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl)
+        if (cbox[sl] >= 0) block12<false>(acc, tk + sl * kR * kR, m[sl]);  // uniform across the CTA
+    float* out = vv + (size_t)(T.lev_off[l] + B * kR) * batch + s;
+#pragma unroll
+    for (int a = 0; a < kR; ++a) out[(size_t)a * batch] = acc[a];
 }
 
 // L2L down to the leaves: leaf-local coefficients L[I] = v^0[I] + sum over the upper
 // levels l of G(l, I mod 2^l) v^l[I >> l], into the leaf-local array the output
-// product reads (leaf I at I R). CTA = (leaf, kTreeThreads signals).
+// product reads (leaf I at I R). CTA = (leaf, kTreeThreads signals); the leaf's chain
+// blocks are staged in shared memory, and each level's coefficients are loaded (contiguous
+// across the warp's signals) while the previous level's product runs.
 __global__ void __launch_bounds__(kTreeThreads) k_far_down(const FarTree T, const float* __restrict__ vv,
-                                                           int64_t ldm, float* __restrict__ lc, int64_t ldl,
-                                                           int64_t batch) {
+                                                           float* __restrict__ lc, int64_t ldl, int64_t batch) {
+    __shared__ __align__(16) float ch[kFarMaxLev][kR * kR];
     const int I = blockIdx.x;
+    for (int e = threadIdx.x; e < (T.nlev - 1) * kR * kR; e += blockDim.x) {
+        const int l = 1 + e / (kR * kR), q = e % (kR * kR);
+        ch[l][q] = __ldg(T.chain + (size_t)(T.chain_off[l] + (I & ((1 << l) - 1))) * kR * kR + q);
+    }
+    __syncthreads();
     const int64_t s = (int64_t)blockIdx.y * kTreeThreads + threadIdx.x;
     if (s >= batch) return;
-    const float* row = vv + s * ldm;
-    float acc[kR];
-    load12(acc, row + (int64_t)I * kR);
+    auto load_level = [&](float (&m)[kR], int l) {
+        const float* src = vv + (size_t)(T.lev_off[l] + (I >> l) * kR) * batch + s;
+#pragma unroll
+        for (int a = 0; a < kR; ++a) m[a] = __ldg(src + (size_t)a * batch);
+    };
+    float acc[kR], m[kR], mn[kR];
+    load_level(acc, 0);
+    if (T.nlev > 1) load_level(m, 1);
 #pragma unroll 1
     for (int l = 1; l < T.nlev; ++l) {
-        float m[kR];
-        load12(m, row + T.lev_off[l] + (int64_t)(I >> l) * kR);
-        block12<false>(acc, T.chain + (size_t)(T.chain_off[l] + (I & ((1 << l) - 1))) * kR * kR, m);
+        if (l + 1 < T.nlev) load_level(mn, l + 1);
+        block12<false>(acc, ch[l], m);
+#pragma unroll
+        for (int a = 0; a < kR; ++a) m[a] = mn[a];
     }
     store12(lc + s * ldl + (int64_t)I * kR, acc);
 }
@@ -652,8 +668,7 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
         k_far_m2l<<<dim3((unsigned)h->nbox, (unsigned)gy), kTreeThreads, 0, st>>>(T, mc, vv, h->ldm, batch);
         note_launch(st, "k_far_m2l", 8.0 * (double)batch * h->ldm, 2.0 * kR * kR * 3.5 * h->nbox * (double)batch);
         DCTPLUS_CUDA_TRY(cudaGetLastError());
-        k_far_down<<<dim3((unsigned)h->nleaf, (unsigned)gy), kTreeThreads, 0, st>>>(T, vv, h->ldm, lc, h->ldl,
-                                                                                    batch);
+        k_far_down<<<dim3((unsigned)h->nleaf, (unsigned)gy), kTreeThreads, 0, st>>>(T, vv, lc, h->ldl, batch);
         note_launch(st, "k_far_down", 4.0 * (double)batch * (h->ldm + h->nc),
                     2.0 * kR * kR * (h->nlev - 1) * h->nleaf * (double)batch);
         DCTPLUS_CUDA_TRY(cudaGetLastError());

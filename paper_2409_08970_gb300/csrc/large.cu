@@ -316,6 +316,10 @@ static dctplus_status launch_r8(int n, const float* x, int64_t ldx, float* s_out
 // floats per leaf of 64 keep the fragment loads conflict-free
 __device__ __forceinline__ int far_phys(int j) { return j + 4 * (j >> 6); }
 
+// At M = 8192 (n = 16384) one signal's FFT buffer and a separate w buffer would
+// take 160 KB, one CTA per SM; w then lives in the FFT buffer instead.
+__host__ __device__ constexpr bool far_alias(int M) { return M >= 8192; }
+
 // DCT-II (as k_dct_r8) plus the hierarchical far field's per-signal inputs:
 //   leaf moments  mc[b][leaf 12 + a] = sum_{jj < 64} S_a(u_jj) z_j s_j, j = 64 leaf + jj
 //                 (P2M: z-weighted Chebyshev interpolation coefficients of the
@@ -323,8 +327,10 @@ __device__ __forceinline__ int far_phys(int j) { return j + 4 * (j >> 6); }
 //   dense rows    dv[b][o] = sum_j W_oj s_j = sum_j g_oj w_j for the rows whose
 //                 eigenvalue lies outside [0, 4] (no angle, so no leaf), with
 //                 g_oj = -a_o / (mu_o - lambda_j) and w_j = z_j s_j.
-// The post-twiddle also writes w_j = z_j s_j into a separate shared buffer
-// (padded by far_phys); the moments are one [rows = (signal, leaf)] x [K = 64] x [N = 12] contraction
+// The post-twiddle also writes w_j = z_j s_j into a shared buffer (padded by
+// far_phys): a separate one, or at n = 16384 the FFT buffer itself, refilled from
+// the s just written (an L2 re-read), which halves the CTA's shared memory so that
+// two CTAs share an SM. The moments are one [rows = (signal, leaf)] x [K = 64] x [N = 12] contraction
 // per CTA on the tensor cores in split TF32 (A_hi B_lo + A_lo B_hi + A_hi B_hi,
 // each k-step accumulated fresh and added in FP32): one m16n8k8 row tile of 16
 // (signal, leaf) rows per warp. The dense rows are read off the same w buffer
@@ -339,14 +345,20 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
     constexpr int NLEAF = M / 32;      // n / 64
     constexpr int kPost = (M / 2 + TPS) / TPS;
     constexpr int kWps = (TPS + 31) / 32;  // warps (or the part of one) per signal
+    constexpr bool kAlias = far_alias(M);  // w over the FFT buffer
+    static_assert(!kAlias || WB <= 2 * BUF, "w must fit in the FFT buffer");
     extern __shared__ __align__(16) float2 dsm[];
     const int spc = blockDim.x / TPS;
     const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float2* buf = dsm + slot * BUF;
-    float* wall = reinterpret_cast<float*>(dsm + spc * BUF);  // [spc][WB]: w = z s
-    float* wb = wall + slot * WB;
-    float* tqs = wall + spc * WB;                              // [2][64][kFarTqLd]: hi, lo
+    // w = z s of slot sl: [spc][WB] after the FFT buffers, or the slot's FFT buffer
+    float* wall = reinterpret_cast<float*>(dsm + spc * BUF);
+    auto wslot = [&](int sl) -> float* {
+        return kAlias ? reinterpret_cast<float*>(dsm + sl * BUF) : wall + sl * WB;
+    };
+    float* wb = wslot(slot);
+    float* tqs = kAlias ? wall : wall + spc * WB;              // [2][64][kFarTqLd]: hi, lo
     float* tms = tqs + 2 * 64 * kFarTqLd;                      // [2][24][kFarTqLd]: hi, lo
     float* red = tms + 2 * 24 * kFarTqLd;                      // [spc][kWps][2]
     const float2* __restrict__ tw_split = tw + M;
@@ -386,11 +398,18 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                 for (int e = 0; e < 4; ++e) {
                     if (!use[e]) continue;
                     ss[pos[e]] = val[e];
-                    wb[far_phys(pos[e])] = __ldg(F.zf + pos[e]) * val[e];
+                    if (!kAlias) wb[far_phys(pos[e])] = __ldg(F.zf + pos[e]) * val[e];
                 }
             }
         }
         __syncthreads();
+        if constexpr (kAlias) {  // every read of the FFT buffer is done: refill it with w = z s
+            if (live) {
+                const float* ss = s + sig * lds;
+                for (int j = t; j < n; j += TPS) wb[far_phys(j)] = __ldg(F.zf + j) * ss[j];
+            }
+            __syncthreads();
+        }
         if (F.nout > 0) {  // dense rows: sum_j g_oj w_j over the signal's threads
             if (live) {
                 for (int j = t; j < n; j += TPS) {
@@ -410,11 +429,13 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                 red[(slot * kWps + t / 32) * 2 + 1] = d1;
             }
         }
-        if (warp < ntile) {  // P2M: rows (signal slot, leaf) 16 w .. 16 w + 15
-            const int g = lane >> 2, tg = lane & 3;
+        // P2M: rows (signal slot, leaf) 16 w .. 16 w + 15 of this warp
+        float acc[2][4] = {};
+        int64_t rsig[2] = {-1, -1};
+        int rleaf[2] = {0, 0};
+        const int g = lane >> 2, tg = lane & 3;
+        if (warp < ntile) {
             const float* wrow[2];
-            int64_t rsig[2];
-            int rleaf[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = 16 * warp + g + 8 * h;
@@ -422,10 +443,9 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                 rleaf[h] = r % NLEAF;
                 rsig[h] = base + sl_;
                 const bool ok = sl_ < spc && rsig[h] < batch;
-                wrow[h] = ok ? wall + sl_ * WB + rleaf[h] * 68 : nullptr;
+                wrow[h] = ok ? wslot(sl_) + rleaf[h] * 68 : nullptr;
                 if (!ok) rsig[h] = -1;
             }
-            float acc[2][4] = {};
 #pragma unroll 1
             for (int ks = 0; ks < 8; ++ks) {
                 const int k0 = 8 * ks + tg;
@@ -444,6 +464,10 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                     for (int e = 0; e < 4; ++e) acc[nt][e] += d[e];
                 }
             }
+        }
+        // with w over the FFT buffer, the moments may overwrite it only once every warp has read it
+        if constexpr (kAlias) __syncthreads();
+        if (warp < ntile) {
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -534,7 +558,8 @@ static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_ou
         grid = std::min<int64_t>(grid, (batch + spc - 1) / spc);
     }
     smem = (size_t)spc * sizeof(float2) * (M + M / 8) +
-           sizeof(float) * ((size_t)spc * (2 * M + M / 8) + 2 * 64 * kFarTqLd + 2 * 24 * kFarTqLd + spc * kWps * 2);
+           sizeof(float) * ((far_alias(M) ? 0 : (size_t)spc * (2 * M + M / 8)) + 2 * 64 * kFarTqLd +
+                            2 * 24 * kFarTqLd + spc * kWps * 2);
     static bool attr[64] = {};
     if (!attr[dev & 63]) {
         DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_dct_far<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
