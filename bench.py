@@ -111,6 +111,36 @@ def roofline_of(recs, hbm_peak, bf16_peak, peak_src):
     return roof
 
 
+_ORACLE_PLANS = {}
+
+
+def oracle_plan(n, v, rho, roots=None):
+    """The oracle's plan for (n, v, rho[, sampled roots]), built once per bench run (its
+    secular solve is O(n^2) per root set in FP64 on the host)."""
+    from oracle import cauchy
+    key = (n, float(rho), np.asarray(v, dtype=np.float64).tobytes(),
+           None if roots is None else tuple(int(r) for r in roots))
+    if key not in _ORACLE_PLANS:
+        _ORACLE_PLANS[key] = (cauchy.make_plan(n, v, rho) if roots is None
+                              else cauchy.make_plan(n, v, rho, roots=roots))
+    return _ORACLE_PLANS[key]
+
+
+def oracle_rate(fn, samples_per_call, sample, budget_s=1.0):
+    """The FP64 oracle timed as it stands on the host cores: fn() repeated for about budget_s
+    seconds (plan creation excluded), as input samples per second."""
+    calls = 0
+    t0 = time.perf_counter()
+    while True:
+        fn()
+        calls += 1
+        elapsed = time.perf_counter() - t0
+        if elapsed >= budget_s:
+            break
+    return {"value": calls * samples_per_call / elapsed / 1e9, "unit": "GSamples/s",
+            "cores": len(os.sched_getaffinity(0)), "kind": "oracle", "sample": sample}
+
+
 def oracle_error(n, v, rho, x, y, sig_rows=8, root_sample=None, seed=7):
     """FP32 output against the FP64 oracle (Cauchy formula) on a sampled subset of signals: all
     rows up to n = 4096, else about 40 sampled secular-root rows. Errors relative to the
@@ -120,14 +150,14 @@ def oracle_error(n, v, rho, x, y, sig_rows=8, root_sample=None, seed=7):
     sig = np.sort(rng.choice(x.shape[0], min(sig_rows, x.shape[0]), replace=False))
     xs = x[sig].astype(np.float64)
     if n <= 4096 and root_sample is None:
-        op = cauchy.make_plan(n, v, rho)
+        op = oracle_plan(n, v, rho)
         cols = np.arange(n)
     else:
-        probe = cauchy.make_plan(n, v, rho, roots=[])
+        probe = oracle_plan(n, v, rho, roots=[])
         K = int(probe.row_kind.sum())
         roots = np.unique(np.concatenate([rng.choice(K, min(K, root_sample or 36), replace=False),
                                           [0, K - 1]]))
-        op = cauchy.make_plan(n, v, rho, roots=roots)
+        op = oracle_plan(n, v, rho, roots=roots)
         cols = np.nonzero((op.row_kind == 1) & np.isin(op.row_index, roots))[0]
     ref = cauchy.transform(op, xs, rows=cols)
     got = y[sig][:, cols].astype(np.float64)
@@ -473,6 +503,13 @@ def bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, er
         out[name] = entry
         for p in plans:
             p.close()
+    if errors and n <= 4096:  # the oracle beside it (rho = 2.0; all coefficients of k signals)
+        from oracle import cauchy
+        op = oracle_plan(n, v, 2.0)
+        k = max(4, min(256, (1 << 26) // (n * n)))
+        xs = xh[:k].astype(np.float64)
+        out["cpu_oracle"] = oracle_rate(lambda: cauchy.transform(op, xs), k * n,
+                                        f"{k} signals, all {n} coefficients, one plan (rho = 2.0)")
     if n > 64:  # what the autotuner measures and would pick for this n and batch (rho = 2.0)
         t = pkg.dctplus_autotune(n, v, 2.0, batch, None, sh)
         out["autotune"] = {"choice": {1: "dense", 2: "hierarchical", 3: "cuda_core"}.get(t["cauchy_mode"]),
@@ -505,9 +542,11 @@ def bench_fp64_n64(pkg, torch, dev, stream, args, flush, peaks):
     recs = trace_kernels(pkg, torch, stream, step, flush)
     step()
     torch.cuda.synchronize()
-    ref = cauchy.transform(cauchy.make_plan(n, v, 1.0), xh)
+    op = cauchy.make_plan(n, v, 1.0)
+    ref = cauchy.transform(op, xh)
     got = y.cpu().numpy()
     rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    cpu = oracle_rate(lambda: cauchy.transform(op, xh), batch * n, f"the whole batch ({batch} signals)")
     k = recs[0]
     achieved = k["flops"] / (k["ms"] * 1e-3) / 1e12
     plan.close()
@@ -517,6 +556,7 @@ def bench_fp64_n64(pkg, torch, dev, stream, args, flush, peaks):
             "dtype": "f64", "plan_ms": plan_ms,
             "err_vs_fp64_oracle": {"max_abs": float(np.abs(got - ref).max()),
                                    "normwise_rel_max": float(rel.max())},
+            "cpu_oracle": cpu,
             "roofline": {"bound": "alu", "kernel": k["kernel"], "kernel_ms": k["ms"],
                          "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_NOMINAL_TFLOPS,
@@ -585,6 +625,13 @@ def bench_pruned(pkg, torch, dev, stream, args, flush, peaks, n=512, batch=16384
             "max_abs_rel_to_signal_norm": err,
             "sample": f"{len(sig)} signals x {m_out} coefficients x {len(ops)} updates"
                       + ("" if c_p == n else "; against the oracle's Theorem 3.4 truncated block")}
+        xs = xh[sig].astype(np.float64)
+        if c_p == n:
+            fn = lambda: [cauchy.transform(op, xs, rows=np.arange(m_out)) for op in ops]
+        else:
+            fn = lambda: [cauchy.pruned_transform(op, xs, m_out, c_p) for op in ops]
+        out[name]["cpu_oracle"] = oracle_rate(fn, len(sig) * n,
+                                              f"{len(sig)} signals, {len(ops)} updates, {m_out} coefficients each")
 
     def full():
         for p, yy in zip(plans, ys):
@@ -646,13 +693,17 @@ def bench_backward(pkg, torch, dev, stream, args, flush, peaks, n=1024, batch=81
            "grad_v_rel": float(np.linalg.norm(g_v.cpu().numpy() - r_v) / np.linalg.norm(r_v)),
            "sample": "gx on 8 signals; grad_rho and grad_v over the whole batch (the oracle's "
                      "gradients for the same upstream g)"}
+    xs, gs = xh[:64], gh[:64]
+    cpu = oracle_rate(lambda: (cauchy.transform(op, xs), gradient.backward_x(op, gs),
+                               gradient.parameter_gradients(op, xs, gs)), 64 * n,
+                      "64 signals: forward, then the gradients to x, rho and v")
     plan.close()
     return {"workload": f"n={n}, batch {batch}, loss = sum y[:, {n // 2}:]^2, dense unit v (seed 1), "
                         "rho = 2.0; forward + backward to x, rho, v",
             "value": samples / (t_ms * 1e-3) / 1e9, "unit": "GSamples/s (forward + backward)",
             "ms_per_step": t_ms, "launches_per_step": launches, "plan_ms": plan_ms,
             "roofline": roofline_of(recs, hbm_peak, bf16_peak, peak_src),
-            "fp32_err_vs_fp64_oracle": err}
+            "fp32_err_vs_fp64_oracle": err, "cpu_oracle": cpu}
 
 
 def bench_dense_gft(pkg, torch, dev, stream, args, flush, wl, plans, seg):

@@ -125,6 +125,24 @@ def test_far_field_forms_agree_and_default(pkg):
         pkg.Plan(1024, self_loop_v(1024, 0), 1.0, cauchy_mode=pkg.CAUCHY_HIER, far_field=3)
 
 
+@pytest.mark.parametrize("far_field", [1, 2])
+def test_hierarchical_unaligned_input_view(pkg, far_field):
+    """x as a view offset by one element (ld = n + 1, not 16-byte aligned): the DCT kernel
+    reads it with scalar loads instead of float4; the result must not change."""
+    n, batch = 1024, 130
+    v = random_unit_v(n)
+    xo = normal_signals(batch, n + 1, seed=11)
+    big = torch.tensor(xo, dtype=torch.float32, device="cuda")
+    ref = cauchy.transform(cauchy.make_plan(n, v, 2.0), xo[:, 1:])
+    plan = pkg.Plan(n, v, 2.0, cauchy_mode=pkg.CAUCHY_HIER, far_field=far_field)
+    y = plan.forward(big[:, 1:]).double().cpu().numpy()
+    assert relerr(y, ref).max() < F32_TOL
+    y2 = run32(plan, xo[:, 1:])  # the same rows, contiguous and aligned
+    assert np.abs(y - y2).max() <= 1e-6 * np.abs(y2).max()
+    plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
+
+
 def test_hierarchical_n16384_sampled(pkg):
     n, batch = 16384, 512
     v = random_unit_v(n)

@@ -94,3 +94,39 @@ def test_route_size_limit(pkg):
         with pytest.raises(pkg.DctPlusError) as e:
             pkg.Plan(n, self_loop_v(n, 0), 1.0, cauchy_mode=pkg.CAUCHY_NFST)
         assert e.value.status == 2
+
+
+def test_fast_route_edge_cases(pkg):
+    """The O(n log n) kernel on an empty batch, on input views that are strided and not
+    16-byte aligned (ld = n + 3, offset by three elements), with rho = 0 (every row deflated,
+    so the result is the DCT-II itself), and on a batch much larger than its grid (each CTA
+    loops over many signals)."""
+    for n in (64, 1024):
+        v = random_unit_v(n, seed=5)
+        op = cauchy.make_plan(n, v, 0.9)
+        plan = pkg.Plan(n, v, 0.9, cauchy_mode=pkg.CAUCHY_NFST)
+        assert plan.forward(torch.zeros((0, n), dtype=torch.float64, device="cuda")).shape == (0, n)
+        xo = normal_signals(7, n + 3, seed=4)
+        big = torch.tensor(xo, dtype=torch.float64, device="cuda")
+        y = plan.forward(big[:, 3:]).cpu().numpy()
+        ref = cauchy.transform(op, xo[:, 3:])
+        tol = max(1e-12, 1e-13 * n / conditioning(op))
+        e = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert e.max() < 2 * tol, (n, e.max())
+        plan.close()
+        zero = pkg.Plan(n, v, 0.0, cauchy_mode=pkg.CAUCHY_NFST)
+        x = normal_signals(9, n, seed=6)
+        y = zero.forward(torch.tensor(x, dtype=torch.float64, device="cuda")).cpu().numpy()
+        assert np.abs(y - scipy.fft.dct(x, norm="ortho", axis=1)).max() < 1e-13 * np.abs(x).sum(axis=1).max()
+        zero.close()
+    n, batch = 16, 20000
+    v = random_unit_v(n, seed=9)
+    op = cauchy.make_plan(n, v, 1.3)
+    plan = pkg.Plan(n, v, 1.3, cauchy_mode=pkg.CAUCHY_NFST)
+    x = normal_signals(batch, n, seed=10)
+    y = plan.forward(torch.tensor(x, dtype=torch.float64, device="cuda")).cpu().numpy()
+    ref = cauchy.transform(op, x)
+    tol = max(1e-12, 1e-13 * n / conditioning(op))
+    assert (np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() < 2 * tol
+    plan.close()
+    assert pkg.dctplus_sync_check(0) == 0

@@ -99,3 +99,18 @@ def test_autotune_cache_record_and_lookup(tmp_path):
     assert pkg.dctplus_tune_lookup(path, "other device", 1024, 4096) is None
     with pytest.raises(pkg.DctPlusError):
         pkg.dctplus_tune_record(path, dev, 1024, 4096, 9, 0, 0.1)                 # bad mode
+
+
+def test_oracle_plans_are_cached_and_timed_without_planning():
+    """The bench builds each oracle plan once per (n, v, rho, roots) and times the oracle's
+    transform alone; the rate counts input samples per second."""
+    n = 64
+    v = random_unit_v(n)
+    a = bench.oracle_plan(n, v, 2.0)
+    assert bench.oracle_plan(n, v, 2.0) is a
+    assert bench.oracle_plan(n, v, -0.3) is not a
+    assert bench.oracle_plan(n, v, 2.0, roots=[0, 1]) is not a
+    calls = []
+    r = bench.oracle_rate(lambda: calls.append(1), 1000, "stub", budget_s=0.05)
+    assert r["kind"] == "oracle" and r["unit"] == "GSamples/s" and r["cores"] >= 1
+    assert r["value"] > 0 and len(calls) >= 1
