@@ -536,7 +536,7 @@ __device__ __forceinline__ void block12(float (&acc)[kR], const float* T, const 
 // CTA = (box, kTreeThreads signals); the box's slot blocks are staged in shared memory.
 // The output is coefficient-major, vv[(lev_off[l] + B R + a) batch + s], so that a warp's
 // stores (and k_far_down's loads) are contiguous across its signals.
-__global__ void __launch_bounds__(kTreeThreads) k_far_m2l(const FarTree T, const float* __restrict__ mc,
+__global__ void __launch_bounds__(kTreeThreads, 3) k_far_m2l(const FarTree T, const float* __restrict__ mc,
                                                           float* __restrict__ vv, int64_t ldm, int64_t batch) {
     __shared__ __align__(16) float tk[4 * kR * kR];
     __shared__ int cbox[4];
@@ -551,13 +551,14 @@ __global__ void __launch_bounds__(kTreeThreads) k_far_m2l(const FarTree T, const
     if (s >= batch) return;
     float acc[kR] = {};
     const float* row = mc + s * ldm + T.lev_off[l];
-    float m[4][kR];
 #pragma unroll
-    for (int sl = 0; sl < 4; ++sl)  // all four loads in flight before the products
-        if (cbox[sl] >= 0) load12(m[sl], row + (int64_t)cbox[sl] * kR);
-#pragma unroll
-    for (int sl = 0; sl < 4; ++sl)
-        if (cbox[sl] >= 0) block12<false>(acc, tk + sl * kR * kR, m[sl]);  // uniform across the CTA
+    for (int sl = 0; sl < 4; ++sl) {  // one list entry at a time; three CTAs per SM hide the loads
+        const int Cb = cbox[sl];
+        if (Cb < 0) continue;  // uniform across the CTA
+        float m[kR];
+        load12(m, row + (int64_t)Cb * kR);
+        block12<false>(acc, tk + sl * kR * kR, m);
+    }
     float* out = vv + (size_t)(T.lev_off[l] + B * kR) * batch + s;
 #pragma unroll
     for (int a = 0; a < kR; ++a) out[(size_t)a * batch] = acc[a];
