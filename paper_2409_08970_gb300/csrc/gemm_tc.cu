@@ -27,15 +27,17 @@
 // Optional second output: the TF32 remainder of Y (for a Y that feeds another
 // split-TF32 product).
 //
-// Tiles 128 x 128, persistent CTAs (one per SM), 448 threads:
+// Tiles 128 x BN (BN = 128, or 64 for products with few tiles), persistent CTAs
+// (one per SM), 448 threads:
 //   warp 0      TMA producer: A_hi, (A_lo,) B_hi, B_lo K-slices of 32 (3 stages)
-//   warp 1      TMEM owner (256 columns: two 128-column chunk buffers), MMA issuer
+//   warp 1      TMEM owner (2 BN columns: two chunk buffers), MMA issuer
 //   warps 2..9  chunk promotion into registers, final store; two warps per
-//               TMEM lane quarter, 64 columns each. A warp writes its 32 x 64
-//               block as two 32 x 32 boxes staged in its own 4 KB of shared
-//               memory and stored by TMA (rows past M are clipped): stores of
-//               rows straight from registers would put 32 partial-sector L2
-//               writes per instruction into the load/store unit.
+//               TMEM lane quarter, BN / 2 columns each. A warp writes its
+//               32 x BN / 2 block as 32 x 32 boxes staged in its own 4 KB of
+//               shared memory and stored by TMA (rows past M are clipped):
+//               stores of rows straight from registers would put 32
+//               partial-sector L2 writes per instruction into the load/store
+//               unit.
 //   warps 10..13 A_lo of each landed stage whose source has no A_lo array,
 //               written next to A_hi in the same swizzled layout (the
 //               remainder is elementwise, so the byte offsets are A_hi's).
@@ -56,24 +58,37 @@ namespace dctplus {
 
 namespace gemm {
 
-constexpr int kBM = 128, kBN = 128, kBK = 32;
+constexpr int kBM = 128, kBK = 32;
 constexpr int kStages = 3;
 constexpr int kThreads = 448;
 constexpr uint32_t kWaitLimit = 1u << 22;
-constexpr uint32_t kSlice = kBM * kBK * 4;           // 16 KB: one 128 x 32 FP32 slice
-constexpr uint32_t kStageBytes = 4 * kSlice;          // A_hi, A_lo, B_hi, B_lo
-constexpr uint32_t kOffY = kStages * kStageBytes;     // 8 warps x 4 KB output staging
-constexpr uint32_t kOffBar = kOffY + 8 * 4096;
-constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;
+constexpr uint32_t kSlice = kBM * kBK * 4;  // 16 KB: one 128 x 32 FP32 A slice
 
-constexpr int kMaxTilesN = 128;
+// Shared-memory layout and TMEM use of a tile 128 x BN (BN = 128 or 64): per stage
+// A_hi, A_lo (16 KB each), B_hi, B_lo (BN x 32 FP32 each), then the output staging
+// (8 warps x 4 KB) and the barriers; two BN-column TMEM chunk buffers; each of the 8
+// epilogue warps owns BN / 2 columns of its lane quarter.
+template <int BN>
+struct Tile {
+    static_assert(BN == 64 || BN == 128, "tile width");
+    static constexpr uint32_t kSliceB = BN * kBK * 4;
+    static constexpr uint32_t kOffAlo = kSlice, kOffBhi = 2 * kSlice, kOffBlo = 2 * kSlice + kSliceB;
+    static constexpr uint32_t kStageBytes = 2 * kSlice + 2 * kSliceB;
+    static constexpr uint32_t kOffY = kStages * kStageBytes;
+    static constexpr uint32_t kOffBar = kOffY + 8 * 4096;
+    static constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;
+    static constexpr int kTmemCols = 2 * BN;
+    static constexpr int kWarpCols = BN / 2;
+};
+
+constexpr int kMaxTilesN = 256;
 constexpr int kMaxSrc = 2;
 constexpr int kMaxSeg = 8;
 constexpr int kTabStride = 2 + 4 * kMaxSeg;  // per column tile: nseg, nk, {src, a_col, b_col, nch} x kMaxSeg
-static_assert(kTabStride == kGemmTabStride && kMaxSeg == kGemmMaxSeg && kBN == kGemmBN, "table layout");
+static_assert(kTabStride == kGemmTabStride && kMaxSeg == kGemmMaxSeg, "table layout");
 
 struct Src {
-    CUtensorMap a_hi, a_lo, b_hi, b_lo;  // A: [M x Ka], B: [N x Kb], FP32, box 32 x 128
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;  // A: [M x Ka] box 32 x 128, B: [N x Kb] box 32 x BN, FP32
 };
 
 struct Params {
@@ -100,11 +115,13 @@ __device__ __forceinline__ float tf32_rem(float v) {
     return __uint_as_float(ptx::cvt_rna_tf32(v - __uint_as_float(__float_as_uint(v) & ~0x1FFFu)));
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ Params P) {
+    using T = Tile<BN>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + T::kOffBar);
     uint64_t* full = bars + 0;        // [kStages]
     uint64_t* empty = bars + 4;       // [kStages]
     uint64_t* acc_full = bars + 8;    // [2]
@@ -131,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         ptx::fence_mbar_init();
     }
     if (warp == 1) {
-        ptx::tmem_alloc(tmem_slot, 256);
+        ptx::tmem_alloc(tmem_slot, T::kTmemCols);
         ptx::tmem_relinquish();
         ptx::tc_fence_before();
     }
@@ -144,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         if (lane == 0) {
             int it = 0, issued = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int m0 = (t / P.tiles_n) * kBM, tn = t % P.tiles_n, n0 = tn * kBN;
+                const int m0 = (t / P.tiles_n) * kBM, tn = t % P.tiles_n, n0 = tn * BN;
                 const int* tab = P.tab ? P.tab + tn * kTabStride : nullptr;
                 const int nseg = tab ? __ldg(tab) : 1;
                 for (int sg = 0; sg < nseg && ok; ++sg) {
@@ -160,12 +177,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     for (int kc = 0; kc < nch; ++kc, ++it) {
                         const int s = it % kStages;
                         if (!ptx::mbar_wait(&empty[s], ((it / kStages) & 1) ^ 1, kWaitLimit)) { ok = false; break; }
-                        unsigned char* st = sm + s * kStageBytes;
-                        ptx::mbar_expect_tx(&full[s], chip ? kStageBytes - kSlice : kStageBytes);
-                        ptx::tma_load_2d(st + 0 * kSlice, &S.a_hi, acol + kc * kBK, m0, &full[s]);
-                        if (!chip) ptx::tma_load_2d(st + 1 * kSlice, &S.a_lo, acol + kc * kBK, m0, &full[s]);
-                        ptx::tma_load_2d(st + 2 * kSlice, &S.b_hi, bcol + kc * kBK, n0, &full[s]);
-                        ptx::tma_load_2d(st + 3 * kSlice, &S.b_lo, bcol + kc * kBK, n0, &full[s]);
+                        unsigned char* st = sm + s * T::kStageBytes;
+                        ptx::mbar_expect_tx(&full[s], chip ? T::kStageBytes - kSlice : T::kStageBytes);
+                        ptx::tma_load_2d(st, &S.a_hi, acol + kc * kBK, m0, &full[s]);
+                        if (!chip) ptx::tma_load_2d(st + T::kOffAlo, &S.a_lo, acol + kc * kBK, m0, &full[s]);
+                        ptx::tma_load_2d(st + T::kOffBhi, &S.b_hi, bcol + kc * kBK, n0, &full[s]);
+                        ptx::tma_load_2d(st + T::kOffBlo, &S.b_lo, bcol + kc * kBK, n0, &full[s]);
                         issued = it + 1;
                     }
                 }
@@ -178,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_tf32(kBM, kBN);
+            constexpr uint32_t idesc = ptx::idesc_tf32(kBM, BN);
             const uint64_t d0 = ptx::desc_sw128(ptx::smem_u32(sm));
             int it = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -189,10 +206,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     if (!ptx::mbar_wait(&full[s], (it / kStages) & 1, kWaitLimit)) { ok = false; break; }
                     if (!ptx::mbar_wait(&lo_full[s], (it / kStages) & 1, kWaitLimit)) { ok = false; break; }
                     ptx::tc_fence_after();
-                    const uint32_t d = tmem + b * kBN;
-                    const uint64_t ds = d0 + (uint64_t)(s * (kStageBytes >> 4));
-                    const uint64_t ahi = ds, alo = ds + (kSlice >> 4), bhi = ds + 2 * (kSlice >> 4),
-                                   blo = ds + 3 * (kSlice >> 4);
+                    const uint32_t d = tmem + b * BN;
+                    const uint64_t ds = d0 + (uint64_t)(s * (T::kStageBytes >> 4));
+                    const uint64_t ahi = ds, alo = ds + (T::kOffAlo >> 4), bhi = ds + (T::kOffBhi >> 4),
+                                   blo = ds + (T::kOffBlo >> 4);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) ptx::mma_tf32(d, ahi + 2 * k, blo + 2 * k, idesc, k > 0);
 #pragma unroll
@@ -224,8 +241,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     const int s = it % kStages;
                     if (!ptx::mbar_wait(&full[s], (it / kStages) & 1, kWaitLimit)) { ok = false; break; }
                     if (chip) {
-                        const float4* hi = reinterpret_cast<const float4*>(sm + s * kStageBytes);
-                        float4* lo = reinterpret_cast<float4*>(sm + s * kStageBytes + kSlice);
+                        const float4* hi = reinterpret_cast<const float4*>(sm + s * T::kStageBytes);
+                        float4* lo = reinterpret_cast<float4*>(sm + s * T::kStageBytes + T::kOffAlo);
 #pragma unroll
                         for (int e = 0; e < (int)(kSlice / 16 / 128); ++e) {
                             const float4 v = hi[ct + 128 * e];
@@ -242,22 +259,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     } else {
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int r = 32 * q + lane;
-        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + 64 * h;
-        float acc[64];
+        constexpr int WC = T::kWarpCols;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + WC * h;
+        float acc[WC];
         uint32_t u[16];
         int it = 0;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int m0 = (t / P.tiles_n) * kBM, n0 = (t % P.tiles_n) * kBN;
+            const int m0 = (t / P.tiles_n) * kBM, n0 = (t % P.tiles_n) * BN;
             const int nk = tile_chunks(P, t % P.tiles_n);
 #pragma unroll
-            for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+            for (int j = 0; j < WC; ++j) acc[j] = 0.f;
             for (int kc = 0; kc < nk; ++kc, ++it) {
                 const int b = it & 1;
                 if (!ptx::mbar_wait(&acc_full[b], (it >> 1) & 1, kWaitLimit)) { ok = false; break; }
                 ptx::tc_fence_after();
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    ptx::tmem_ld16(tl + b * kBN + 16 * j, u);
+                for (int j = 0; j < WC / 16; ++j) {
+                    ptx::tmem_ld16(tl + b * BN + 16 * j, u);
                     ptx::tmem_wait_ld();
 #pragma unroll
                     for (int e = 0; e < 16; ++e) acc[16 * j + e] += __uint_as_float(u[e]);
@@ -267,10 +285,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                 if (lane == 0) ptx::mbar_arrive(&acc_empty[b]);
             }
             if (!ok) break;
-            unsigned char* ys = sm + kOffY + (warp - 2) * 4096;
+            unsigned char* ys = sm + T::kOffY + (warp - 2) * 4096;
             for (int part = 0; part < 1 + P.has_lo; ++part) {
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
+                for (int c = 0; c < WC / 32; ++c) {
                     // the previous box from this buffer has been read by its store
                     if (lane == 0) ptx::bulk_wait_group_read0();
                     __syncwarp();
@@ -284,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
                     ptx::fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        ptx::tma_store_2d(part ? &P.ylo_map : &P.y_map, n0 + 64 * h + 32 * c, m0 + 32 * q, ys);
+                        ptx::tma_store_2d(part ? &P.ylo_map : &P.y_map, n0 + WC * h + 32 * c, m0 + 32 * q, ys);
                         ptx::bulk_commit_group();
                     }
                 }
@@ -297,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (warp == 1) ptx::tmem_dealloc(tmem, 256);
+    if (warp == 1) ptx::tmem_dealloc(tmem, T::kTmemCols);
 }
 
 }  // namespace gemm
@@ -334,24 +352,39 @@ static bool encode_rows(CUtensorMap* m, const float* base, int64_t rows, int64_t
 
 static bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 
+template <int BN>
 static dctplus_status gemm_attr(int dev) {
     static bool attr[64] = {};
     if (!attr[dev & 63]) {
-        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(gemm::k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)gemm::kSmemBytes));
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(gemm::k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)gemm::Tile<BN>::kSmemBytes));
         attr[dev & 63] = true;
     }
     return DCTPLUS_OK;
 }
 
-static bool encode_src(gemm::Src* d, int* lo_chip, const GemmSrc& g, int M, int N) {
+static bool encode_src(gemm::Src* d, int* lo_chip, const GemmSrc& g, int M, int N, int bn) {
     *lo_chip = g.a_lo ? 0 : 1;
     return encode_rows(&d->a_hi, g.a_hi, M, g.Ka, g.lda) &&
            (!g.a_lo || encode_rows(&d->a_lo, g.a_lo, M, g.Ka, g.lda)) &&
-           encode_rows(&d->b_hi, g.b_hi, N, g.Kb, g.ldb) && encode_rows(&d->b_lo, g.b_lo, N, g.Kb, g.ldb);
+           encode_rows(&d->b_hi, g.b_hi, N, g.Kb, g.ldb, bn) && encode_rows(&d->b_lo, g.b_lo, N, g.Kb, g.ldb, bn);
 }
 
-static dctplus_status gemm_run(gemm::Params& P, float* y, float* y_lo, int64_t ldy, int M, int N,
+template <int BN>
+static dctplus_status gemm_run_bn(gemm::Params& P, cudaStream_t s, int dev, const char* name, double bytes,
+                                  double flops) {
+    dctplus_status r = gemm_attr<BN>(dev);
+    if (r != DCTPLUS_OK) return r;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = std::min(P.tiles_m * P.tiles_n, std::max(sms, 1));
+    gemm::k_gemm_tc<BN><<<grid, gemm::kThreads, gemm::Tile<BN>::kSmemBytes, s>>>(P);
+    note_launch(s, name, bytes, flops);
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+static dctplus_status gemm_run(gemm::Params& P, float* y, float* y_lo, int64_t ldy, int M, int N, int bn,
                                cudaStream_t s, int dev, const char* name, double bytes, double flops) {
     if ((ldy & 3) || !aligned16(y) || (y_lo && !aligned16(y_lo))) return DCTPLUS_ERR_UNSUPPORTED;
     if (!encode_rows(&P.y_map, y, M, N, ldy, 32)) return DCTPLUS_ERR_CUDA;
@@ -360,17 +393,9 @@ static dctplus_status gemm_run(gemm::Params& P, float* y, float* y_lo, int64_t l
     P.M = M;
     P.N = N;
     P.tiles_m = (M + gemm::kBM - 1) / gemm::kBM;
-    P.tiles_n = N / gemm::kBN;
+    P.tiles_n = N / bn;
     P.err = device_error_word(dev);
-    dctplus_status r = gemm_attr(dev);
-    if (r != DCTPLUS_OK) return r;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = std::min(P.tiles_m * P.tiles_n, std::max(sms, 1));
-    gemm::k_gemm_tc<<<grid, gemm::kThreads, gemm::kSmemBytes, s>>>(P);
-    note_launch(s, name, bytes, flops);
-    DCTPLUS_CUDA_TRY(cudaGetLastError());
-    return DCTPLUS_OK;
+    return bn == 64 ? gemm_run_bn<64>(P, s, dev, name, bytes, flops) : gemm_run_bn<128>(P, s, dev, name, bytes, flops);
 }
 
 // y[M x N] = (a_hi + a_lo)[:, band] (b_hi + b_lo)^T (a_lo null: formed on chip
@@ -384,24 +409,25 @@ dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t
                                    int64_t ldy, int M, int N, int K, const int* kbeg,
                                    cudaStream_t s, int dev) {
     if (M <= 0) return DCTPLUS_OK;
-    if (K % gemm::kBK || N % gemm::kBN || (lda & 3) || (ldb & 3) || N / gemm::kBN > gemm::kMaxTilesN)
+    constexpr int bn = kGemmBN;
+    if (K % gemm::kBK || N % bn || (lda & 3) || (ldb & 3) || N / bn > gemm::kMaxTilesN)
         return DCTPLUS_ERR_UNSUPPORTED;
     gemm::Params P;
     memset(&P, 0, sizeof(P));
     GemmSrc g{a_hi, a_lo, lda, Ka, b_hi, b_lo, ldb, K};
-    if (!encode_src(&P.src[0], &P.lo_chip[0], g, M, N)) return DCTPLUS_ERR_CUDA;
+    if (!encode_src(&P.src[0], &P.lo_chip[0], g, M, N, bn)) return DCTPLUS_ERR_CUDA;
     P.K = K;
     P.tab = nullptr;
-    const int tiles_n = N / gemm::kBN;
+    const int tiles_n = N / bn;
     for (int t = 0; t < tiles_n; ++t) {
         P.kbeg[t] = kbeg ? kbeg[t] : 0;
         if (P.kbeg[t] & 3) return DCTPLUS_ERR_UNSUPPORTED;
     }
     // A (and its stored remainder) read once over the columns the tiles use, B hi and lo
     // once, Y written
-    const double bytes = (a_lo ? 8.0 : 4.0) * (double)M * std::min(Ka, K + (tiles_n - 1) * gemm::kBN) +
+    const double bytes = (a_lo ? 8.0 : 4.0) * (double)M * std::min(Ka, K + (tiles_n - 1) * bn) +
                          8.0 * (double)N * K + 4.0 * (double)M * N;
-    return gemm_run(P, y, nullptr, ldy, M, N, s, dev, "k_gemm_tc", bytes, 6.0 * (double)M * N * K);
+    return gemm_run(P, y, nullptr, ldy, M, N, bn, s, dev, "k_gemm_tc", bytes, 6.0 * (double)M * N * K);
 }
 
 // The same product with a segment table (see the kernel's header): `tab` is a
@@ -411,9 +437,10 @@ dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t
 // the TF32 remainder of y.
 dctplus_status launch_gemm_tc_segs(const GemmSrc* srcs, int nsrc, const int* tab, int64_t chunks_total,
                                    double a_cols, float* y, float* y_lo, int64_t ldy, int M, int N,
-                                   cudaStream_t s, int dev, const char* name) {
+                                   cudaStream_t s, int dev, const char* name, int bn) {
     if (M <= 0) return DCTPLUS_OK;
-    if (nsrc < 1 || nsrc > gemm::kMaxSrc || !tab || N % gemm::kBN || N / gemm::kBN > gemm::kMaxTilesN)
+    if ((bn != 64 && bn != 128) || nsrc < 1 || nsrc > gemm::kMaxSrc || !tab || N % bn ||
+        N / bn > gemm::kMaxTilesN)
         return DCTPLUS_ERR_UNSUPPORTED;
     gemm::Params P;
     memset(&P, 0, sizeof(P));
@@ -423,15 +450,15 @@ dctplus_status launch_gemm_tc_segs(const GemmSrc* srcs, int nsrc, const int* tab
         if ((g.lda & 3) || (g.ldb & 3) || !aligned16(g.a_hi) || (g.a_lo && !aligned16(g.a_lo)) ||
             !aligned16(g.b_hi) || !aligned16(g.b_lo))
             return DCTPLUS_ERR_UNSUPPORTED;
-        if (!encode_src(&P.src[i], &P.lo_chip[i], g, M, N)) return DCTPLUS_ERR_CUDA;
+        if (!encode_src(&P.src[i], &P.lo_chip[i], g, M, N, bn)) return DCTPLUS_ERR_CUDA;
         b_bytes += 8.0 * (double)N * g.Kb;
         a_bytes_per_col += g.a_lo ? 8.0 : 4.0;
     }
     P.tab = tab;
     P.K = 0;
-    const double flops = 6.0 * (double)M * gemm::kBN * gemm::kBK * (double)chunks_total;
+    const double flops = 6.0 * (double)M * bn * gemm::kBK * (double)chunks_total;
     const double bytes = a_bytes_per_col / nsrc * (double)M * a_cols + b_bytes + (y_lo ? 8.0 : 4.0) * (double)M * N;
-    return gemm_run(P, y, y_lo, ldy, M, N, s, dev, name, bytes, flops);
+    return gemm_run(P, y, y_lo, ldy, M, N, bn, s, dev, name, bytes, flops);
 }
 
 }  // namespace dctplus

@@ -49,6 +49,14 @@ namespace dctplus {
 
 constexpr int kLeaf = 64;
 constexpr int kR = 12;  // Chebyshev degree of the far-field expansions
+// The leaf-to-leaf product's N (12 n / 64, padded to 128) gives few 128-column tiles at
+// small n (32 row tiles x 2 at n = 1024, batch 4096). When even twice as many 64-column
+// tiles fit in one wave over the SMs it runs 64 wide (measured: 14.3 -> 12.1 us at
+// n = 1024); otherwise 128 wide, since narrow tiles cost more per multiply-add (at
+// n = 4096, batch 4096: 45 -> 57 us; at n = 16384, batch 512, where 96 wide tiles leave
+// SMs idle but each runs K = 3072: 80 -> 139 us). Its table has the same entry for every
+// tile, so one table of 64-column tiles serves both widths.
+constexpr int kL2lNarrow = 64;
 
 struct HierTables {
     int nleaf = 0, Kw = 0;
@@ -411,14 +419,14 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
                 kf_lo[(size_t)ia * ncp + jb] = tf32_host((float)(v - (double)hi));
             }
         }
-        tab_l2l.assign((size_t)(ncp / 128) * kGemmTabStride, 0);
-        for (int t = 0; t < ncp / 128; ++t) {
+        tab_l2l.assign((size_t)(ncp / kL2lNarrow) * kGemmTabStride, 0);
+        for (int t = 0; t < ncp / kL2lNarrow; ++t) {
             int* e = &tab_l2l[(size_t)t * kGemmTabStride];
             e[0] = 1;
             e[1] = (nc + 31) / 32;  // columns past nc of the kernel samples are zero
             e[5] = (nc + 31) / 32;
         }
-        h->chunks_l2l = (int64_t)(ncp / 128) * ((nc + 31) / 32);
+        h->chunks_l2l = (int64_t)(ncp / kGemmBN) * ((nc + 31) / 32);  // per 128 columns of N
     }
     // dense rows for eigenvalues outside [0, 4]: W_oj = g_oj z_j with g_oj = -a_o / (mu_o - lambda_j)
     std::vector<float> outg((size_t)std::max(h->nout, 1) * n, 0.0f);
@@ -649,8 +657,12 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     if (r != DCTPLUS_OK) return r;
     if (!tree) {
         GemmSrc l2l{mc, nullptr, h->ldm, h->nc, h->kf_hi, h->kf_lo, h->ncp, h->ncp};
-        r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l, (double)h->nc, lc, nullptr, h->ldl,
-                                (int)batch, h->ncp, st, p->device, "k_gemm_tc");
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+        const int64_t wide_tiles = (batch + 127) / 128 * (h->ncp / kGemmBN);
+        const int bn = 2 * wide_tiles <= sms ? kL2lNarrow : kGemmBN;
+        r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l * (kGemmBN / bn), (double)h->nc, lc, nullptr,
+                                h->ldl, (int)batch, h->ncp, st, p->device, "k_gemm_tc", bn);
         if (r != DCTPLUS_OK) return r;
     } else {
         FarTree T;

@@ -169,10 +169,10 @@ struct GemmSrc {
 };
 constexpr int kGemmTabStride = 34;  // ints per column tile of a segment table
 constexpr int kGemmMaxSeg = 8;
-constexpr int kGemmBN = 128;         // output columns per tile
+constexpr int kGemmBN = 128;         // output columns per tile (bn: 128, or 64 for products with few tiles)
 dctplus_status launch_gemm_tc_segs(const GemmSrc* srcs, int nsrc, const int* tab, int64_t chunks_total,
                                    double a_cols, float* y, float* y_lo, int64_t ldy, int M, int N,
-                                   cudaStream_t s, int dev, const char* name);
+                                   cudaStream_t s, int dev, const char* name, int bn = kGemmBN);
 
 // pruned.cu
 void pruned_forget(dctplus_plan_t p);  // drop cached stacked tables that use p

@@ -143,6 +143,27 @@ def test_hierarchical_unaligned_input_view(pkg, far_field):
     assert pkg.dctplus_sync_check(0) == 0
 
 
+def test_leaf_to_leaf_product_widths_agree(pkg):
+    """The leaf-level far field's product runs 64 columns wide when its 128-wide tiles would not
+    cover the SMs (small batches) and 128 wide otherwise: n = 2048 with 8192 signals takes the
+    wide tiles, the first 1000 of them alone the narrow ones. Both agree with each other and
+    with the Cauchy formula on sampled signals."""
+    n = 2048
+    v = random_unit_v(n)
+    x = normal_signals(8192, n, seed=13)
+    plan = pkg.Plan(n, v, 2.0, cauchy_mode=pkg.CAUCHY_HIER, far_field=1)
+    y_wide = run32(plan, x)
+    y_narrow = run32(plan, x[:1000])
+    assert np.abs(y_wide[:1000] - y_narrow).max() <= 1e-6 * np.abs(y_narrow).max()
+    rng = np.random.default_rng(4)
+    sig = np.sort(rng.choice(1000, 24, replace=False))
+    ref = cauchy.transform(cauchy.make_plan(n, v, 2.0), x[sig])
+    assert relerr(y_wide[sig], ref).max() < F32_TOL
+    assert relerr(y_narrow[sig], ref).max() < F32_TOL
+    plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
+
+
 def test_hierarchical_n16384_sampled(pkg):
     n, batch = 16384, 512
     v = random_unit_v(n)
