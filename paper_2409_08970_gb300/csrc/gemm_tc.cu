@@ -403,15 +403,21 @@ static dctplus_status gemm_run(gemm::Params& P, float* y, float* y_lo, int64_t l
 // [N x K]; output column tile tn uses A columns kbeg[tn] .. kbeg[tn] + K - 1
 // (nullptr kbeg: all zero, the plain product with Ka = K). K % 32 == 0,
 // N % 128 == 0, kbeg multiples of 4, 16-byte aligned bases, leading
-// dimensions multiples of 4 floats.
+// dimensions multiples of 4 floats. kbeg is per 128-column tile; without it a
+// small product runs in 64-column tiles.
 dctplus_status launch_gemm_tc_band(const float* a_hi, const float* a_lo, int64_t lda, int Ka,
                                    const float* b_hi, const float* b_lo, int64_t ldb, float* y,
                                    int64_t ldy, int M, int N, int K, const int* kbeg,
                                    cudaStream_t s, int dev) {
     if (M <= 0) return DCTPLUS_OK;
-    constexpr int bn = kGemmBN;
-    if (K % gemm::kBK || N % bn || (lda & 3) || (ldb & 3) || N / bn > gemm::kMaxTilesN)
+    if (K % gemm::kBK || N % kGemmBN || (lda & 3) || (ldb & 3) || N / kGemmBN > gemm::kMaxTilesN)
         return DCTPLUS_ERR_UNSUPPORTED;
+    // 64-column tiles when even twice as many tiles fit in one wave over the SMs (small
+    // products: dense n = 256, batch 4096, has 64 tiles of 128 x 128), else 128 columns
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t wide_tiles = (int64_t)((M + gemm::kBM - 1) / gemm::kBM) * (N / kGemmBN);
+    const int bn = !kbeg && 2 * wide_tiles <= sms ? 64 : kGemmBN;
     gemm::Params P;
     memset(&P, 0, sizeof(P));
     GemmSrc g{a_hi, a_lo, lda, Ka, b_hi, b_lo, ldb, K};
