@@ -676,12 +676,19 @@ dctplus_status launch_nfst_fast_n(dctplus_plan_t p, const T* x, int64_t ldx, T* 
                                   int64_t batch, cudaStream_t st) {
     constexpr int NT = nfst_threads(N);
     const size_t smem = sizeof(double2) * (size_t)(N + (N - 1) / 8 + 1);
-    DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_nfst_fast<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-    int sms = 0, per_sm = 0;
+    // per device, once: the shared-memory opt-in and the resident CTAs per SM it allows
+    static int per_sm_dev[64] = {};
+    int& per_sm = per_sm_dev[p->device & 63];
+    if (per_sm == 0) {
+        DCTPLUS_CUDA_TRY(cudaFuncSetAttribute(k_nfst_fast<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        int r = 0;
+        DCTPLUS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_nfst_fast<T, N>, NT, smem));
+        per_sm = std::max(r, 1);
+    }
+    int sms = 0;
     DCTPLUS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-    DCTPLUS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nfst_fast<T, N>, NT, smem));
-    const int64_t grid = std::min<int64_t>(batch, (int64_t)std::max(sms, 1) * std::max(per_sm, 1));
+    const int64_t grid = std::min<int64_t>(batch, (int64_t)std::max(sms, 1) * per_sm);
     NfstFastArgs a;
     a.S = p->d_sin;
     a.f = p->nfst->f;
