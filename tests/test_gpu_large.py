@@ -183,11 +183,13 @@ def test_hierarchical_n16384_sampled(pkg):
     assert pkg.dctplus_sync_check(0) == 0
 
 
+@pytest.mark.parametrize("n", [1024, 4096])
 @pytest.mark.parametrize("far_field", [1, 2])
-def test_hierarchical_full_batch_sampled(pkg, far_field):
-    """n = 1024, batch 4096 in the hierarchical mode: the launch configuration the benchmark
-    times, checked on 128 sampled signals against the Cauchy formula."""
-    n, batch = 1024, 4096
+def test_hierarchical_full_batch_sampled(pkg, far_field, n):
+    """n = 1024 and 4096, batch 4096 in the hierarchical mode: the launch configurations the
+    benchmark times (at n = 4096 the leaf-to-leaf product takes its 128-wide tiles), checked on
+    128 sampled signals against the Cauchy formula."""
+    batch = 4096
     v = random_unit_v(n)
     x = normal_signals(batch, n, seed=0)
     for rho in (-0.3, 2.0):
@@ -201,9 +203,10 @@ def test_hierarchical_full_batch_sampled(pkg, far_field):
     assert pkg.dctplus_sync_check(0) == 0
 
 
-def test_dense_mode_full_batch_sampled(pkg):
-    """n = 1024, batch 4096: the launch configuration the benchmark times."""
-    n, batch = 1024, 4096
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_dense_mode_full_batch_sampled(pkg, n):
+    """n = 1024 and 4096, batch 4096: the launch configurations the benchmark times."""
+    batch = 4096
     v = random_unit_v(n)
     x = normal_signals(batch, n, seed=0)
     for rho in (-0.3, 2.0):

@@ -130,3 +130,27 @@ def test_fast_route_edge_cases(pkg):
     assert (np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() < 2 * tol
     plan.close()
     assert pkg.dctplus_sync_check(0) == 0
+
+
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_fast_route_full_batch_sampled(pkg, n):
+    """The route in the benchmark's launch configuration (batch 4096, FP32 data, two updates),
+    checked on sampled signals against the oracle's route and the Cauchy formula."""
+    batch = 4096
+    x = normal_signals(batch, n, seed=0)
+    rng = np.random.default_rng(5)
+    sig = np.sort(rng.choice(batch, 12, replace=False))
+    for rho in (-0.3, 2.0):
+        v = random_unit_v(n)
+        op = cauchy.make_plan(n, v, rho)
+        plan = pkg.Plan(n, v, rho, cauchy_mode=pkg.CAUCHY_NFST)
+        y = plan.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()[sig]
+        tol = max(1e-12, 1e-13 * n / conditioning(op))
+        same = nfst_route.transform(op, x[sig])
+        ref = cauchy.transform(op, x[sig])
+        e_same = np.linalg.norm(y - same, axis=1) / np.linalg.norm(same, axis=1)
+        e_ref = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert e_same.max() < max(1e-6, 2 * tol), (n, rho, e_same.max())  # FP32 output rounding
+        assert e_ref.max() < max(1e-6, 2 * tol), (n, rho, e_ref.max())
+        plan.close()
+    assert pkg.dctplus_sync_check(0) == 0
