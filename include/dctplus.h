@@ -173,6 +173,25 @@ dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const v
                                int64_t ldx, void* y_dev, int64_t ldy, int64_t batch,
                                dctplus_stream_t stream);
 
+/* Several updates of one graph over the same signals: y_k = X_k^T x for the
+ * `count` plans (same n and device), FP32. Algorithm 1 step 1, the DCT-II
+ * s = U^T x, does not depend on the update (v, rho), so plans in the
+ * hierarchical mode share it (one DCT per group of up to 4 plans, each plan's
+ * far-field inputs formed from the same s), and plans in the dense mode share
+ * it before their own products; other sets (and a set listing one plan twice)
+ * run plan by plan.
+ *   x_dev : batch rows of n floats, row stride ldx >= n.
+ *   y_dev : batch rows, row stride ldy >= count * n; plan k's coefficients at
+ *           columns k n .. k n + n - 1 (ascending eigenvalue). Must not
+ *           overlap x.
+ * Results equal those of dctplus_execute per plan. Asynchronous on `stream`;
+ * uses the plans' stream workspaces (plan 0's holds the shared s), so calls
+ * that share a plan and a stream must not overlap.
+ * Errors: INVALID_ARG (null or mixed plans, count < 1, strides too small,
+ * misaligned or overlapping buffers), the errors of dctplus_execute. */
+dctplus_status dctplus_execute_multi(const dctplus_plan_t* plans, int count, const float* x_dev, int64_t ldx,
+                                     float* y_dev, int64_t ldy, int64_t batch, dctplus_stream_t stream);
+
 /* Same transform with HOST buffers: copies x to the device, transforms, copies
  * y back, all on `stream`, and returns after the stream has finished. Pinned
  * host memory gives full copy bandwidth. Uses a device staging buffer owned by

@@ -108,6 +108,15 @@ def dctplus_execute_pruned(handles, x_ptr: int, ldx: int, y_ptr: int, ldy: int, 
     check(st, "dctplus_execute_pruned")
 
 
+def dctplus_execute_multi(handles, x_ptr: int, ldx: int, y_ptr: int, ldy: int, batch: int,
+                          stream: int) -> None:
+    """Several plans of one length over the same FP32 signals; plan k's coefficients at columns
+    k n .. k n + n - 1 of each output row (ldy >= len(handles) n)."""
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    st = _lib.load().dctplus_execute_multi(arr, len(handles), x_ptr, int(ldx), y_ptr, int(ldy), int(batch), stream)
+    check(st, "dctplus_execute_multi")
+
+
 def dctplus_backward(handle, gy_ptr: int, ldg: int, y_ptr: int, ldy: int, gx_ptr: int, ldgx: int,
                      grad_rho_ptr: int, grad_v_ptr: int, batch: int, stream: int) -> None:
     st = _lib.load().dctplus_backward(handle, gy_ptr, int(ldg), y_ptr or None, int(ldy), gx_ptr or None,

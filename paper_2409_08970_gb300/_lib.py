@@ -37,7 +37,7 @@ SEG_WORDS = 3
 EXPORTS = (
     "dctplus_plan", "dctplus_destroy", "dctplus_plan_inspect", "dctplus_plan_size",
     "dctplus_plan_cauchy_mode", "dctplus_plan_far_field", "dctplus_execute", "dctplus_execute_host",
-    "dctplus_execute_noalloc", "dctplus_execute_pruned", "dctplus_backward",
+    "dctplus_execute_noalloc", "dctplus_execute_pruned", "dctplus_execute_multi", "dctplus_backward",
     "dctplus_group_create", "dctplus_group_destroy", "dctplus_execute_group",
     "dctplus_execute_group_host", "dctplus_sync_check", "dctplus_launch_count",
     "dctplus_status_string", "dctplus_trace_begin", "dctplus_trace_end", "dctplus_autotune",
@@ -81,6 +81,7 @@ def load():
         "dctplus_execute_host": (c_int, [vp, c_int, vp, vp, i64, vp]),
         "dctplus_execute_noalloc": (c_int, [vp, vp, i64, vp, i64, i64, vp]),
         "dctplus_execute_pruned": (c_int, [vp, c_int, vp, i64, vp, i64, i64, c_int, c_int, vp]),
+        "dctplus_execute_multi": (c_int, [vp, c_int, vp, i64, vp, i64, i64, vp]),
         "dctplus_backward": (c_int, [vp, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp]),
         "dctplus_group_create": (c_int, [ctypes.POINTER(vp), c_int, vp]),
         "dctplus_group_destroy": (None, [vp]),

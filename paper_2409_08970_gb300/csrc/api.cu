@@ -406,6 +406,61 @@ dctplus_status dctplus_execute(dctplus_plan_t p, dctplus_dtype dtype, const void
     return launch_large_f32(p, x, ldx, y, ldy, batch, s);
 }
 
+dctplus_status dctplus_execute_multi(const dctplus_plan_t* plans, int count, const float* x_dev, int64_t ldx,
+                                     float* y_dev, int64_t ldy, int64_t batch, dctplus_stream_t stream) {
+    if (!plans || count < 1 || batch < 0) return DCTPLUS_ERR_INVALID_ARG;
+    for (int k = 0; k < count; ++k)
+        if (!plans[k] || plans[k]->n != plans[0]->n || plans[k]->device != plans[0]->device)
+            return DCTPLUS_ERR_INVALID_ARG;
+    const int n = plans[0]->n;
+    if (batch == 0) return DCTPLUS_OK;
+    if (!x_dev || !y_dev || ldx < n || ldy < (int64_t)count * n) return DCTPLUS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 3) return DCTPLUS_ERR_INVALID_ARG;
+    {  // reject overlapping x / y ranges
+        const uintptr_t xa = (uintptr_t)x_dev, ya = (uintptr_t)y_dev;
+        const uintptr_t xe = xa + 4 * (size_t)((batch - 1) * ldx + n);
+        const uintptr_t ye = ya + 4 * (size_t)((batch - 1) * ldy + (int64_t)count * n);
+        if (xa < ye && ya < xe) return DCTPLUS_ERR_INVALID_ARG;
+    }
+    dctplus_status st = check_device(plans[0]->device);
+    if (st != DCTPLUS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    bool all_hier = n > kSmallMax && (n & (n - 1)) == 0, all_dense = all_hier;
+    for (int k = 0; k < count; ++k) {
+        all_hier = all_hier && plans[k]->cauchy_mode == DCTPLUS_CAUCHY_HIER && plans[k]->hier;
+        all_dense = all_dense && plans[k]->cauchy_mode == DCTPLUS_CAUCHY_DENSE && plans[k]->d_whi;
+        // a handle given twice would share its workspace between two of the group's slots
+        for (int j = 0; j < k; ++j) all_hier = all_hier && plans[j] != plans[k];
+    }
+    const bool y_ok = (reinterpret_cast<uintptr_t>(y_dev) & 15) == 0 && (ldy & 3) == 0 && batch <= INT32_MAX;
+    if (all_hier && y_ok) {
+        // one DCT-II per group of up to kFarMaxPlans plans, every plan's far field and output after it
+        for (int k0 = 0; k0 < count; k0 += kFarMaxPlans) {
+            const int K = std::min(kFarMaxPlans, count - k0);
+            float* ys[kFarMaxPlans];
+            for (int k = 0; k < K; ++k) ys[k] = y_dev + (int64_t)(k0 + k) * n;
+            if ((st = launch_hier_multi(plans + k0, K, x_dev, ldx, ys, ldy, batch, s)) != DCTPLUS_OK) return st;
+        }
+        return DCTPLUS_OK;
+    }
+    if (all_dense && y_ok) {
+        // one DCT-II, then each plan's dense product from the same s
+        float* ws = static_cast<float*>(plan_workspace(plans[0], s, sizeof(float) * (size_t)batch * n));
+        if (!ws) return DCTPLUS_ERR_CUDA;
+        if ((st = launch_dct_fft(plans[0], x_dev, ldx, ws, n, batch, s)) != DCTPLUS_OK) return st;
+        for (int k = 0; k < count; ++k)
+            if ((st = launch_gemm_tc(ws, nullptr, n, plans[k]->d_whi, plans[k]->d_wlo, n, y_dev + (int64_t)k * n, ldy,
+                                     (int)batch, n, n, s, plans[k]->device)) != DCTPLUS_OK)
+                return st;
+        return DCTPLUS_OK;
+    }
+    for (int k = 0; k < count; ++k)
+        if ((st = dctplus_execute(plans[k], DCTPLUS_F32, x_dev, ldx, y_dev + (int64_t)k * n, ldy, batch, stream)) !=
+            DCTPLUS_OK)
+            return st;
+    return DCTPLUS_OK;
+}
+
 dctplus_status dctplus_execute_host(dctplus_plan_t p, dctplus_dtype dtype, const void* x_host,
                                     void* y_host, int64_t batch, dctplus_stream_t stream) {
     if (!p || batch < 0 || (batch > 0 && (!x_host || !y_host))) return DCTPLUS_ERR_INVALID_ARG;

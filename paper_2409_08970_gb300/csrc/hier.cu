@@ -623,27 +623,29 @@ void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes);
 //      against the tile's window of leaf-local coefficients (far field), then
 //      the dense rows' slots; y is written once.
 // The TF32 remainders of every GEMM operand are formed on chip.
-dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
-                           int64_t batch, cudaStream_t st) {
+namespace {
+
+// A plan's share of the hierarchical product: its workspace (moments, the tree's M2L output,
+// leaf-local coefficients with the dense-row slots) and the DCT-kernel inputs that go with it.
+struct HierRun {
+    float* mc = nullptr;
+    float* vv = nullptr;
+    float* lc = nullptr;
+    DctFar far{};
+};
+
+dctplus_status hier_prepare(dctplus_plan_t p, float* ws, int64_t batch, HierRun* R) {
     HierTables* h = p->hier;
-    const int n = p->n;
-    if (!h || batch > INT32_MAX || (reinterpret_cast<uintptr_t>(y) & 15) || (ldy & 3))
-        return DCTPLUS_ERR_UNSUPPORTED;
-    if (batch <= 0) return DCTPLUS_OK;
     const bool tree = h->form == 2;
-    const size_t plane = (size_t)batch * n, mplane = (size_t)batch * h->ldm, lplane = (size_t)batch * h->ldl;
-    float* ws = static_cast<float*>(
-        plan_workspace(p, st, sizeof(float) * (plane + (tree ? 2 : 1) * mplane + lplane)));
-    if (!ws) return DCTPLUS_ERR_CUDA;
-    float* s_hi = ws;
-    float* mc = ws + plane;
-    float* vv = tree ? mc + mplane : nullptr;
-    float* lc = mc + (tree ? 2 : 1) * mplane;
-    DctFar far;
+    const size_t mplane = (size_t)batch * h->ldm;
+    R->mc = ws;
+    R->vv = tree ? ws + mplane : nullptr;
+    R->lc = ws + (tree ? 2 : 1) * mplane;
+    DctFar& far = R->far;
     far.zf = h->zf;
     far.tq_hi = h->tq_hi;
     far.tq_lo = h->tq_lo;
-    far.mc = mc;
+    far.mc = R->mc;
     far.ldm = h->ldm;
     far.tm_hi = h->tm_hi;
     far.tm_lo = h->tm_lo;
@@ -651,17 +653,25 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     for (int l = 0; l < kFarMaxLev; ++l) far.lev_off[l] = h->lev_off[l];
     far.out_g = h->out_g;
     far.nout = h->nout;
-    far.dv = lc + h->dslot;
+    far.dv = R->lc + h->dslot;
     far.ldd = h->ldl;
-    dctplus_status r = launch_dct_far(p, x, ldx, s_hi, n, batch, far, st);
-    if (r != DCTPLUS_OK) return r;
-    if (!tree) {
-        GemmSrc l2l{mc, nullptr, h->ldm, h->nc, h->kf_hi, h->kf_lo, h->ncp, h->ncp};
+    return DCTPLUS_OK;
+}
+
+// Far field (leaf-to-leaf product or the tree's M2L and downward passes) and the output
+// product of one plan, from the shared s.
+dctplus_status hier_finish(dctplus_plan_t p, const HierRun& R, const float* s_hi, float* y, int64_t ldy,
+                           int64_t batch, cudaStream_t st) {
+    HierTables* h = p->hier;
+    const int n = p->n;
+    dctplus_status r = DCTPLUS_OK;
+    if (h->form != 2) {
+        GemmSrc l2l{R.mc, nullptr, h->ldm, h->nc, h->kf_hi, h->kf_lo, h->ncp, h->ncp};
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
         const int64_t wide_tiles = (batch + 127) / 128 * (h->ncp / kGemmBN);
         const int bn = 2 * wide_tiles <= sms ? kL2lNarrow : kGemmBN;
-        r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l * (kGemmBN / bn), (double)h->nc, lc, nullptr,
+        r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l * (kGemmBN / bn), (double)h->nc, R.lc, nullptr,
                                 h->ldl, (int)batch, h->ncp, st, p->device, "k_gemm_tc", bn);
         if (r != DCTPLUS_OK) return r;
     } else {
@@ -678,18 +688,58 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
         for (int l = 0; l <= kFarMaxLev; ++l) T.box_off[l] = h->box_off[l];
         const int64_t gy = (batch + kTreeThreads - 1) / kTreeThreads;
         if (gy > 65535) return DCTPLUS_ERR_UNSUPPORTED;
-        k_far_m2l<<<dim3((unsigned)h->nbox, (unsigned)gy), kTreeThreads, 0, st>>>(T, mc, vv, h->ldm, batch);
+        k_far_m2l<<<dim3((unsigned)h->nbox, (unsigned)gy), kTreeThreads, 0, st>>>(T, R.mc, R.vv, h->ldm, batch);
         note_launch(st, "k_far_m2l", 8.0 * (double)batch * h->ldm, 2.0 * kR * kR * 3.5 * h->nbox * (double)batch);
         DCTPLUS_CUDA_TRY(cudaGetLastError());
-        k_far_down<<<dim3((unsigned)h->nleaf, (unsigned)gy), kTreeThreads, 0, st>>>(T, vv, lc, h->ldl, batch);
+        k_far_down<<<dim3((unsigned)h->nleaf, (unsigned)gy), kTreeThreads, 0, st>>>(T, R.vv, R.lc, h->ldl, batch);
         note_launch(st, "k_far_down", 4.0 * (double)batch * (h->ldm + h->nc),
                     2.0 * kR * kR * (h->nlev - 1) * h->nleaf * (double)batch);
         DCTPLUS_CUDA_TRY(cudaGetLastError());
     }
     GemmSrc out[2] = {{s_hi, nullptr, n, n, h->slab_hi, h->slab_lo, h->Kw, h->Kw},
-                      {lc, nullptr, h->ldl, h->ldl, h->ext_hi, h->ext_lo, h->Kx + 32, h->Kx + 32}};
+                      {R.lc, nullptr, h->ldl, h->ldl, h->ext_hi, h->ext_lo, h->Kx + 32, h->Kx + 32}};
     return launch_gemm_tc_segs(out, 2, h->tab_out, h->chunks_out, h->acols_out, y, nullptr, ldy,
                                (int)batch, n, st, p->device, "k_gemm_tc");
+}
+
+}  // namespace
+
+dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
+                           int64_t batch, cudaStream_t st) {
+    return launch_hier_multi(&p, 1, x, ldx, &y, ldy, batch, st);
+}
+
+// Several plans of one length over the same signals: one DCT-II (with every plan's moments and
+// dense rows), then each plan's far field and output product into ys[k]. s lives in plan 0's
+// workspace; each plan keeps its own moments and leaf-local coefficients.
+dctplus_status launch_hier_multi(const dctplus_plan_t* plans, int K, const float* x, int64_t ldx,
+                                 float* const* ys, int64_t ldy, int64_t batch, cudaStream_t st) {
+    if (K < 1 || K > kFarMaxPlans || batch > INT32_MAX || (ldy & 3)) return DCTPLUS_ERR_UNSUPPORTED;
+    const int n = plans[0]->n;
+    for (int k = 0; k < K; ++k)
+        if (!plans[k]->hier || plans[k]->n != n || plans[k]->device != plans[0]->device ||
+            (reinterpret_cast<uintptr_t>(ys[k]) & 15))
+            return DCTPLUS_ERR_UNSUPPORTED;
+    if (batch <= 0) return DCTPLUS_OK;
+    HierRun runs[kFarMaxPlans];
+    DctFarSet set;
+    set.K = K;
+    float* s_hi = nullptr;
+    for (int k = 0; k < K; ++k) {
+        HierTables* h = plans[k]->hier;
+        const size_t plane = k == 0 ? (size_t)batch * n : 0;
+        const size_t mplane = (size_t)batch * h->ldm, lplane = (size_t)batch * h->ldl;
+        float* ws = static_cast<float*>(
+            plan_workspace(plans[k], st, sizeof(float) * (plane + (h->form == 2 ? 2 : 1) * mplane + lplane)));
+        if (!ws) return DCTPLUS_ERR_CUDA;
+        if (k == 0) s_hi = ws;
+        dctplus_status r = hier_prepare(plans[k], ws + plane, batch, &runs[k]);
+        if (r != DCTPLUS_OK) return r;
+        set.f[k] = runs[k].far;
+    }
+    dctplus_status r = launch_dct_far_multi(plans[0], x, ldx, s_hi, n, batch, set, st);
+    for (int k = 0; k < K && r == DCTPLUS_OK; ++k) r = hier_finish(plans[k], runs[k], s_hi, ys[k], ldy, batch, st);
+    return r;
 }
 
 }  // namespace dctplus

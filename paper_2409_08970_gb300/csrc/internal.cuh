@@ -155,6 +155,10 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd);
 void free_hier(HierTables* h);
 dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float* y, int64_t ldy,
                            int64_t batch, cudaStream_t st);
+// K <= kFarMaxPlans hierarchical plans of one length over the same signals: one DCT-II,
+// then plan k's output into ys[k] (row stride ldy)
+dctplus_status launch_hier_multi(const dctplus_plan_t* plans, int K, const float* x, int64_t ldx,
+                                 float* const* ys, int64_t ldy, int64_t batch, cudaStream_t st);
 
 // gemm_tc.cu: split-TF32 tensor-core product y = A B^T over K segments
 struct GemmSrc {
@@ -169,6 +173,10 @@ struct GemmSrc {
 };
 constexpr int kGemmTabStride = 34;  // ints per column tile of a segment table
 constexpr int kGemmMaxSeg = 8;
+// y[M x N] = (a_hi + a_lo) (b_hi + b_lo)^T, K columns (a_lo null: formed on chip)
+dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda, const float* b_hi,
+                              const float* b_lo, int64_t ldb, float* y, int64_t ldy, int M, int N, int K,
+                              cudaStream_t s, int dev);
 constexpr int kGemmBN = 128;         // output columns per tile (bn: 128, or 64 for products with few tiles)
 dctplus_status launch_gemm_tc_segs(const GemmSrc* srcs, int nsrc, const int* tab, int64_t chunks_total,
                                    double a_cols, float* y, float* y_lo, int64_t ldy, int M, int N,
@@ -218,10 +226,20 @@ struct DctFar {
     int64_t ldd;
 };
 
+// The far-field inputs of up to kFarMaxPlans plans of one length over the same signals: the
+// DCT-II is formed once, the moments and dense rows per plan.
+constexpr int kFarMaxPlans = 4;
+struct DctFarSet {
+    int K;
+    DctFar f[kFarMaxPlans];
+};
+
 // large.cu
 // DCT-II with the far-field outputs above (n a power of two in [256, 16384])
 dctplus_status launch_dct_far(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds,
                               int64_t batch, const DctFar& far, cudaStream_t st);
+dctplus_status launch_dct_far_multi(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds,
+                                    int64_t batch, const DctFarSet& far, cudaStream_t st);
 dctplus_status launch_dct_fft(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out,
                               int64_t lds, int64_t batch, cudaStream_t st);
 // DCT-III (inverse of the orthonormal DCT-II), n a power of two in [128, 16384]

@@ -338,7 +338,7 @@ __host__ __device__ constexpr bool far_alias(int M) { return M >= 8192; }
 template <int M>
 __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restrict__ x, int64_t ldx,
                                                  float* __restrict__ s, int64_t lds, int64_t batch,
-                                                 const float2* __restrict__ tw, int vec, const DctFar F) {
+                                                 const float2* __restrict__ tw, int vec, const DctFarSet S) {
     constexpr int TPS = fft_tps(M);
     constexpr int BUF = M + M / 8;
     constexpr int WB = 2 * M + M / 8;  // floats of a signal's w buffer (far_phys(n - 1) < WB)
@@ -364,14 +364,18 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
     const float2* __restrict__ tw_split = tw + M;
     const float2* __restrict__ tw_post = tw + 2 * M + 1;
     const float2* __restrict__ twp = tw + 3 * M + 2;
+    // the P2M and M2M tables depend on n only: plan 0's serve every plan of the set
+    const DctFar& F0 = S.f[0];
+    bool any_tree = false;
+    for (int k = 0; k < S.K; ++k) any_tree = any_tree || S.f[k].nlev > 1;
     for (int e = threadIdx.x; e < 64 * kFarTqLd; e += blockDim.x) {
-        tqs[e] = F.tq_hi[e];
-        tqs[64 * kFarTqLd + e] = F.tq_lo[e];
+        tqs[e] = F0.tq_hi[e];
+        tqs[64 * kFarTqLd + e] = F0.tq_lo[e];
     }
-    if (F.nlev > 1)
+    if (any_tree)
         for (int e = threadIdx.x; e < 24 * kFarTqLd; e += blockDim.x) {
-            tms[e] = F.tm_hi[e];
-            tms[24 * kFarTqLd + e] = F.tm_lo[e];
+            tms[e] = F0.tm_hi[e];
+            tms[24 * kFarTqLd + e] = F0.tm_lo[e];
         }
     const int ntile = (spc * NLEAF + 15) / 16;  // P2M row tiles of this CTA
     for (int64_t base = (int64_t)blockIdx.x * spc; base < batch; base += (int64_t)gridDim.x * spc) {
@@ -381,7 +385,6 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
         if (live) dct_load<M>(buf, x + sig * ldx, t, vec);
         __syncthreads();
         fft_pass<M, M>(buf, t, twp);
-        float d0 = 0.f, d1 = 0.f;  // dense-row partial sums
         if (live) {
             float* ss = s + sig * lds;
 #pragma unroll
@@ -398,147 +401,153 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                 for (int e = 0; e < 4; ++e) {
                     if (!use[e]) continue;
                     ss[pos[e]] = val[e];
-                    if (!kAlias) wb[far_phys(pos[e])] = __ldg(F.zf + pos[e]) * val[e];
+                    if (!kAlias) wb[far_phys(pos[e])] = __ldg(F0.zf + pos[e]) * val[e];
                 }
             }
         }
-        __syncthreads();
-        if constexpr (kAlias) {  // every read of the FFT buffer is done: refill it with w = z s
-            if (live) {
-                const float* ss = s + sig * lds;
-                for (int j = t; j < n; j += TPS) wb[far_phys(j)] = __ldg(F.zf + j) * ss[j];
-            }
+        for (int kp = 0; kp < S.K; ++kp) {  // the plans of the set share s; each has its own z, a, mu
+            const DctFar& F = S.f[kp];
+            float d0 = 0.f, d1 = 0.f;  // dense-row partial sums
+            // the previous plan is done with w, the moments on chip and red (and for the first
+            // plan every read of the FFT buffer is done)
             __syncthreads();
-        }
-        if (F.nout > 0) {  // dense rows: sum_j g_oj w_j over the signal's threads
-            if (live) {
-                for (int j = t; j < n; j += TPS) {
-                    const float wj = wb[far_phys(j)];
-                    d0 = fmaf(__ldg(F.out_g + j), wj, d0);
-                    if (F.nout > 1) d1 = fmaf(__ldg(F.out_g + n + j), wj, d1);
+            if (kAlias || kp > 0) {  // w = z s from the s just written
+                if (live) {
+                    const float* ss = s + sig * lds;
+                    for (int j = t; j < n; j += TPS) wb[far_phys(j)] = __ldg(F.zf + j) * ss[j];
+                }
+                __syncthreads();
+            }
+            if (F.nout > 0) {  // dense rows: sum_j g_oj w_j over the signal's threads
+                if (live) {
+                    for (int j = t; j < n; j += TPS) {
+                        const float wj = wb[far_phys(j)];
+                        d0 = fmaf(__ldg(F.out_g + j), wj, d0);
+                        if (F.nout > 1) d1 = fmaf(__ldg(F.out_g + n + j), wj, d1);
+                    }
+                }
+                constexpr int width = TPS < 32 ? TPS : 32;
+#pragma unroll
+                for (int off = width / 2; off > 0; off >>= 1) {
+                    d0 += __shfl_xor_sync(0xffffffffu, d0, off);
+                    d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+                }
+                if ((t & (width - 1)) == 0) {
+                    red[(slot * kWps + t / 32) * 2 + 0] = d0;
+                    red[(slot * kWps + t / 32) * 2 + 1] = d1;
                 }
             }
-            constexpr int width = TPS < 32 ? TPS : 32;
-#pragma unroll
-            for (int off = width / 2; off > 0; off >>= 1) {
-                d0 += __shfl_xor_sync(0xffffffffu, d0, off);
-                d1 += __shfl_xor_sync(0xffffffffu, d1, off);
-            }
-            if ((t & (width - 1)) == 0) {
-                red[(slot * kWps + t / 32) * 2 + 0] = d0;
-                red[(slot * kWps + t / 32) * 2 + 1] = d1;
-            }
-        }
-        // P2M: rows (signal slot, leaf) 16 w .. 16 w + 15 of this warp
-        float acc[2][4] = {};
-        int64_t rsig[2] = {-1, -1};
-        int rleaf[2] = {0, 0};
-        const int g = lane >> 2, tg = lane & 3;
-        if (warp < ntile) {
-            const float* wrow[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = 16 * warp + g + 8 * h;
-                const int sl_ = r / NLEAF;
-                rleaf[h] = r % NLEAF;
-                rsig[h] = base + sl_;
-                const bool ok = sl_ < spc && rsig[h] < batch;
-                wrow[h] = ok ? wslot(sl_) + rleaf[h] * 68 : nullptr;
-                if (!ok) rsig[h] = -1;
-            }
-#pragma unroll 1
-            for (int ks = 0; ks < 8; ++ks) {
-                const int k0 = 8 * ks + tg;
-                const float af[4] = {wrow[0] ? wrow[0][k0] : 0.f, wrow[1] ? wrow[1][k0] : 0.f,
-                                     wrow[0] ? wrow[0][k0 + 4] : 0.f, wrow[1] ? wrow[1][k0 + 4] : 0.f};
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const int c = 8 * nt + g;
-                    const uint32_t bhi[2] = {__float_as_uint(tqs[k0 * kFarTqLd + c]),
-                                             __float_as_uint(tqs[(k0 + 4) * kFarTqLd + c])};
-                    const uint32_t blo[2] = {__float_as_uint(tqs[64 * kFarTqLd + k0 * kFarTqLd + c]),
-                                             __float_as_uint(tqs[64 * kFarTqLd + (k0 + 4) * kFarTqLd + c])};
-                    float d[4];
-                    ptx::mma_split_tf32(d, af, bhi, blo);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[nt][e] += d[e];
-                }
-            }
-        }
-        // with w over the FFT buffer, the moments may overwrite it only once every warp has read it
-        if constexpr (kAlias) __syncthreads();
-        if (warp < ntile) {
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int h = e >> 1, a = 8 * nt + 2 * tg + (e & 1);
-                    if (a >= kFarR || rsig[h] < 0) continue;
-                    F.mc[rsig[h] * F.ldm + rleaf[h] * kFarR + a] = acc[nt][e];
-                    // the leaf moments stay on chip for M2M (the FFT buffer is free now)
-                    if (F.nlev > 1)
-                        reinterpret_cast<float*>(dsm + (rsig[h] - base) * BUF)[rleaf[h] * kFarR + a] = acc[nt][e];
-                }
-        }
-        __syncthreads();  // the dense rows' partial sums are in red, the leaf moments on chip
-        // M2M: level l moments of parent p = E_0 M(left child) + E_1 M(right child), one
-        // m16n8k8 row tile of (signal slot, parent) rows per warp, K = 24 (both children)
-        for (int l = 1; l < F.nlev; ++l) {
-            const int nb = NLEAF >> l;
-            if (warp < (spc * nb + 15) / 16) {
-                const int g = lane >> 2, tg = lane & 3;
-                const float* arow[2];
-                float* orow[2];
-                int64_t osig[2];
-                int ocol[2];
+            // P2M: rows (signal slot, leaf) 16 w .. 16 w + 15 of this warp
+            float acc[2][4] = {};
+            int64_t rsig[2] = {-1, -1};
+            int rleaf[2] = {0, 0};
+            const int g = lane >> 2, tg = lane & 3;
+            if (warp < ntile) {
+                const float* wrow[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int r = 16 * warp + g + 8 * h;
-                    const int sl_ = r / nb, p = r % nb;
-                    const bool ok = sl_ < spc && base + sl_ < batch;
-                    float* mom = reinterpret_cast<float*>(dsm + sl_ * BUF);
-                    ocol[h] = F.lev_off[l] + p * kFarR;
-                    arow[h] = ok ? mom + F.lev_off[l - 1] + 2 * p * kFarR : nullptr;
-                    orow[h] = ok ? mom + ocol[h] : nullptr;
-                    osig[h] = ok ? base + sl_ : -1;
+                    const int sl_ = r / NLEAF;
+                    rleaf[h] = r % NLEAF;
+                    rsig[h] = base + sl_;
+                    const bool ok = sl_ < spc && rsig[h] < batch;
+                    wrow[h] = ok ? wslot(sl_) + rleaf[h] * 68 : nullptr;
+                    if (!ok) rsig[h] = -1;
                 }
-                float acc[2][4] = {};
-#pragma unroll
-                for (int ks = 0; ks < 3; ++ks) {
+#pragma unroll 1
+                for (int ks = 0; ks < 8; ++ks) {
                     const int k0 = 8 * ks + tg;
-                    const float af[4] = {arow[0] ? arow[0][k0] : 0.f, arow[1] ? arow[1][k0] : 0.f,
-                                         arow[0] ? arow[0][k0 + 4] : 0.f, arow[1] ? arow[1][k0 + 4] : 0.f};
+                    const float af[4] = {wrow[0] ? wrow[0][k0] : 0.f, wrow[1] ? wrow[1][k0] : 0.f,
+                                         wrow[0] ? wrow[0][k0 + 4] : 0.f, wrow[1] ? wrow[1][k0 + 4] : 0.f};
 #pragma unroll
                     for (int nt = 0; nt < 2; ++nt) {
                         const int c = 8 * nt + g;
-                        const uint32_t bhi[2] = {__float_as_uint(tms[k0 * kFarTqLd + c]),
-                                                 __float_as_uint(tms[(k0 + 4) * kFarTqLd + c])};
-                        const uint32_t blo[2] = {__float_as_uint(tms[24 * kFarTqLd + k0 * kFarTqLd + c]),
-                                                 __float_as_uint(tms[24 * kFarTqLd + (k0 + 4) * kFarTqLd + c])};
+                        const uint32_t bhi[2] = {__float_as_uint(tqs[k0 * kFarTqLd + c]),
+                                                 __float_as_uint(tqs[(k0 + 4) * kFarTqLd + c])};
+                        const uint32_t blo[2] = {__float_as_uint(tqs[64 * kFarTqLd + k0 * kFarTqLd + c]),
+                                                 __float_as_uint(tqs[64 * kFarTqLd + (k0 + 4) * kFarTqLd + c])};
                         float d[4];
                         ptx::mma_split_tf32(d, af, bhi, blo);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) acc[nt][e] += d[e];
                     }
                 }
+            }
+            // with w over the FFT buffer, the moments may overwrite it only once every warp has read it
+            if constexpr (kAlias) __syncthreads();
+            if (warp < ntile) {
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int h = e >> 1, a = 8 * nt + 2 * tg + (e & 1);
-                        if (a >= kFarR || osig[h] < 0) continue;
-                        orow[h][a] = acc[nt][e];
-                        F.mc[osig[h] * F.ldm + ocol[h] + a] = acc[nt][e];
+                        if (a >= kFarR || rsig[h] < 0) continue;
+                        F.mc[rsig[h] * F.ldm + rleaf[h] * kFarR + a] = acc[nt][e];
+                        // the leaf moments stay on chip for M2M (the FFT buffer is free now)
+                        if (F.nlev > 1)
+                            reinterpret_cast<float*>(dsm + (rsig[h] - base) * BUF)[rleaf[h] * kFarR + a] = acc[nt][e];
                     }
             }
-            __syncthreads();
-        }
-        if (live) {  // the 32 dense-row slots: values, then zeros
-            for (int o = t; o < 32; o += TPS) {
-                float val = 0.f;
-                if (o < F.nout)
-                    for (int w = 0; w < kWps; ++w) val += red[(slot * kWps + w) * 2 + o];
-                F.dv[sig * F.ldd + o] = val;
+            __syncthreads();  // the dense rows' partial sums are in red, the leaf moments on chip
+            // M2M: level l moments of parent p = E_0 M(left child) + E_1 M(right child), one
+            // m16n8k8 row tile of (signal slot, parent) rows per warp, K = 24 (both children)
+            for (int l = 1; l < F.nlev; ++l) {
+                const int nb = NLEAF >> l;
+                if (warp < (spc * nb + 15) / 16) {
+                    const int g = lane >> 2, tg = lane & 3;
+                    const float* arow[2];
+                    float* orow[2];
+                    int64_t osig[2];
+                    int ocol[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int r = 16 * warp + g + 8 * h;
+                        const int sl_ = r / nb, p = r % nb;
+                        const bool ok = sl_ < spc && base + sl_ < batch;
+                        float* mom = reinterpret_cast<float*>(dsm + sl_ * BUF);
+                        ocol[h] = F.lev_off[l] + p * kFarR;
+                        arow[h] = ok ? mom + F.lev_off[l - 1] + 2 * p * kFarR : nullptr;
+                        orow[h] = ok ? mom + ocol[h] : nullptr;
+                        osig[h] = ok ? base + sl_ : -1;
+                    }
+                    float acc[2][4] = {};
+#pragma unroll
+                    for (int ks = 0; ks < 3; ++ks) {
+                        const int k0 = 8 * ks + tg;
+                        const float af[4] = {arow[0] ? arow[0][k0] : 0.f, arow[1] ? arow[1][k0] : 0.f,
+                                             arow[0] ? arow[0][k0 + 4] : 0.f, arow[1] ? arow[1][k0 + 4] : 0.f};
+#pragma unroll
+                        for (int nt = 0; nt < 2; ++nt) {
+                            const int c = 8 * nt + g;
+                            const uint32_t bhi[2] = {__float_as_uint(tms[k0 * kFarTqLd + c]),
+                                                     __float_as_uint(tms[(k0 + 4) * kFarTqLd + c])};
+                            const uint32_t blo[2] = {__float_as_uint(tms[24 * kFarTqLd + k0 * kFarTqLd + c]),
+                                                     __float_as_uint(tms[24 * kFarTqLd + (k0 + 4) * kFarTqLd + c])};
+                            float d[4];
+                            ptx::mma_split_tf32(d, af, bhi, blo);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[nt][e] += d[e];
+                        }
+                    }
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int h = e >> 1, a = 8 * nt + 2 * tg + (e & 1);
+                            if (a >= kFarR || osig[h] < 0) continue;
+                            orow[h][a] = acc[nt][e];
+                            F.mc[osig[h] * F.ldm + ocol[h] + a] = acc[nt][e];
+                        }
+                }
+                __syncthreads();
+            }
+            if (live) {  // the 32 dense-row slots: values, then zeros
+                for (int o = t; o < 32; o += TPS) {
+                    float val = 0.f;
+                    if (o < F.nout)
+                        for (int w = 0; w < kWps; ++w) val += red[(slot * kWps + w) * 2 + o];
+                    F.dv[sig * F.ldd + o] = val;
+                }
             }
         }
     }
@@ -546,7 +555,7 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
 
 template <int M>
 static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_out, int64_t lds, int64_t batch, const float2* tw, int vec,
-                                 const DctFar& F, cudaStream_t st, int dev) {
+                                 const DctFarSet& F, cudaStream_t st, int dev) {
     constexpr int TPS = fft_tps(M);
     constexpr int kWps = (TPS + 31) / 32;
     int spc;
@@ -567,17 +576,29 @@ static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_ou
         attr[dev & 63] = true;
     }
     k_dct_far<M><<<(unsigned)grid, spc * TPS, smem, st>>>(n, x, ldx, s_out, lds, batch, tw, vec, F);
-    note_launch(st, "k_dct_far",
-                8.0 * batch * n + 4.0 * batch * (n / 64) * kFarR + 4.0 * 32 * batch,
-                dct_flops(n) * batch + 6.0 * kFarR * (double)batch * n + 2.0 * F.nout * (double)batch * n);
+    double bytes = 8.0 * batch * n, flops = dct_flops(n) * batch;  // the DCT-II, once for the set
+    for (int k = 0; k < F.K; ++k) {  // each plan's moments and dense rows
+        bytes += 4.0 * batch * (n / 64) * kFarR + 4.0 * 32 * batch;
+        flops += 6.0 * kFarR * (double)batch * n + 2.0 * F.f[k].nout * (double)batch * n;
+    }
+    note_launch(st, "k_dct_far", bytes, flops);
     DCTPLUS_CUDA_TRY(cudaGetLastError());
     return DCTPLUS_OK;
 }
 
-dctplus_status launch_dct_far(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds, int64_t batch, const DctFar& far, cudaStream_t st) {
+dctplus_status launch_dct_far(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds, int64_t batch, const DctFar& far1, cudaStream_t st) {
+    DctFarSet far;
+    far.K = 1;
+    far.f[0] = far1;
+    return launch_dct_far_multi(p, x, ldx, s_out, lds, batch, far, st);
+}
+
+dctplus_status launch_dct_far_multi(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds,
+                                    int64_t batch, const DctFarSet& far, cudaStream_t st) {
     const int n = p->n;
-    if (!p->d_twiddle || batch > INT32_MAX || far.nout > 2 || far.nlev < 1 || far.nlev > kFarMaxLev)
-        return DCTPLUS_ERR_UNSUPPORTED;
+    if (!p->d_twiddle || batch > INT32_MAX || far.K < 1 || far.K > kFarMaxPlans) return DCTPLUS_ERR_UNSUPPORTED;
+    for (int k = 0; k < far.K; ++k)
+        if (far.f[k].nout > 2 || far.f[k].nlev < 1 || far.f[k].nlev > kFarMaxLev) return DCTPLUS_ERR_UNSUPPORTED;
     if (batch <= 0) return DCTPLUS_OK;
     const int vec = ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ldx & 3) == 0) ? 1 : 0;
     const float2* tw = reinterpret_cast<const float2*>(p->d_twiddle);

@@ -233,3 +233,74 @@ def test_lengths_without_an_fft_match_oracle(pkg, n):
         assert err.max() < F32_TOL, (n, rho, err.max())
         plan.close()
     assert pkg.dctplus_sync_check(0) == 0
+
+
+def run_multi(pkg, plans, x):
+    """dctplus_execute_multi over FP32 signals x: a [batch, len(plans) n] array."""
+    n = plans[0].n
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    y = torch.empty((x.shape[0], len(plans) * n), dtype=torch.float32, device="cuda")
+    pkg.dctplus_execute_multi([p.handle for p in plans], xd.data_ptr(), n, y.data_ptr(), len(plans) * n,
+                              x.shape[0], torch.cuda.current_stream().cuda_stream)
+    return y.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["hier_leaf", "hier_tree", "dense"])
+@pytest.mark.parametrize("n", [256, 1024, 4096])
+def test_execute_multi_matches_plan_by_plan(pkg, n, mode):
+    """Several updates over the same signals in one call: the hierarchical plans share one DCT-II
+    (their moments and dense rows formed from the same s), the dense plans share it before their
+    products. Each plan's block equals its own dctplus_execute, and the first agrees with the
+    Cauchy formula; the batch is ragged for every tile shape."""
+    cm = pkg.CAUCHY_DENSE if mode == "dense" else pkg.CAUCHY_HIER
+    far = {"hier_leaf": 1, "hier_tree": 2, "dense": 0}[mode]
+    cases = [(random_unit_v(n, seed=3), -0.3), (random_unit_v(n, seed=3), 2.0), (self_loop_v(n, 0), 0.7)]
+    plans = [pkg.Plan(n, v, rho, cauchy_mode=cm, far_field=far) for v, rho in cases]
+    x = normal_signals(150, n, seed=17)
+    y = run_multi(pkg, plans, x)
+    for k, p in enumerate(plans):
+        yk = run32(p, x)
+        assert np.abs(y[:, k * n:(k + 1) * n] - yk).max() <= 1e-6 * np.abs(yk).max(), (n, mode, k)
+    v, rho = cases[0]
+    ref = cauchy.transform(cauchy.make_plan(n, v, rho), x[:20])
+    assert relerr(y[:20, :n], ref).max() < F32_TOL
+    for p in plans:
+        p.close()
+    assert pkg.dctplus_sync_check(0) == 0
+
+
+def test_execute_multi_groups_mixed_sets_and_errors(pkg):
+    """Five hierarchical plans take two groups (one DCT per group of four); a set mixing the
+    dense and the hierarchical mode runs plan by plan; bad arguments are refused on the host."""
+    n = 1024
+    rhos = (-0.3, 0.4, 0.9, 2.0, 3.5)
+    plans = [pkg.Plan(n, random_unit_v(n, seed=5), r, cauchy_mode=pkg.CAUCHY_HIER) for r in rhos]
+    x = normal_signals(130, n, seed=19)
+    y = run_multi(pkg, plans, x)
+    for k, p in enumerate(plans):
+        yk = run32(p, x)
+        assert np.abs(y[:, k * n:(k + 1) * n] - yk).max() <= 1e-6 * np.abs(yk).max(), k
+    twice = [plans[1], plans[2], plans[1]]  # a handle given twice runs plan by plan
+    y = run_multi(pkg, twice, x)
+    for k, p in enumerate(twice):
+        yk = run32(p, x)
+        assert np.abs(y[:, k * n:(k + 1) * n] - yk).max() <= 1e-6 * np.abs(yk).max(), k
+    mixed = [plans[0], pkg.Plan(n, random_unit_v(n, seed=6), 1.0, cauchy_mode=pkg.CAUCHY_DENSE)]
+    y = run_multi(pkg, mixed, x)
+    for k, p in enumerate(mixed):
+        yk = run32(p, x)
+        assert np.abs(y[:, k * n:(k + 1) * n] - yk).max() <= 1e-6 * np.abs(yk).max(), k
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yd = torch.empty((x.shape[0], 2 * n), dtype=torch.float32, device="cuda")
+    sh = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(pkg.DctPlusError) as e:  # row stride below count * n
+        pkg.dctplus_execute_multi([p.handle for p in mixed], xd.data_ptr(), n, yd.data_ptr(), n, x.shape[0], sh)
+    assert e.value.status == 1
+    other = pkg.Plan(512, random_unit_v(512), 1.0)
+    with pytest.raises(pkg.DctPlusError) as e:  # lengths differ
+        pkg.dctplus_execute_multi([plans[0].handle, other.handle], xd.data_ptr(), n, yd.data_ptr(), 2 * n,
+                                  x.shape[0], sh)
+    assert e.value.status == 1
+    for p in plans + mixed[1:] + [other]:
+        p.close()
+    assert pkg.dctplus_sync_check(0) == 0
