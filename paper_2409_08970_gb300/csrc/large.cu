@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
     constexpr int NLEAF = M / 32;      // n / 64
     constexpr int kPost = (M / 2 + TPS) / TPS;
     constexpr int kWps = (TPS + 31) / 32;  // warps (or the part of one) per signal
+    constexpr int kJ = 2 * M / TPS;        // coefficients per thread (n = 2 M)
     constexpr bool kAlias = far_alias(M);  // w over the FFT buffer
     static_assert(!kAlias || WB <= 2 * BUF, "w must fit in the FFT buffer");
     extern __shared__ __align__(16) float2 dsm[];
@@ -411,19 +412,35 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
             // the previous plan is done with w, the moments on chip and red (and for the first
             // plan every read of the FFT buffer is done)
             __syncthreads();
-            if (kAlias || kp > 0) {  // w = z s from the s just written
+            // n = 2 M: the loops over a signal's coefficients have a fixed trip count, unrolled so
+            // that each thread keeps several L2 / L1 loads in flight
+            if (kAlias || kp > 0) {  // w = z s from the s just written (L2)
                 if (live) {
                     const float* ss = s + sig * lds;
-                    for (int j = t; j < n; j += TPS) wb[far_phys(j)] = __ldg(F.zf + j) * ss[j];
+#pragma unroll 8
+                    for (int i = 0; i < kJ; ++i) {
+                        const int j = t + i * TPS;
+                        wb[far_phys(j)] = __ldg(F.zf + j) * ss[j];
+                    }
                 }
                 __syncthreads();
             }
             if (F.nout > 0) {  // dense rows: sum_j g_oj w_j over the signal's threads
                 if (live) {
-                    for (int j = t; j < n; j += TPS) {
-                        const float wj = wb[far_phys(j)];
-                        d0 = fmaf(__ldg(F.out_g + j), wj, d0);
-                        if (F.nout > 1) d1 = fmaf(__ldg(F.out_g + n + j), wj, d1);
+                    if (F.nout > 1) {
+#pragma unroll 8
+                        for (int i = 0; i < kJ; ++i) {
+                            const int j = t + i * TPS;
+                            const float wj = wb[far_phys(j)];
+                            d0 = fmaf(__ldg(F.out_g + j), wj, d0);
+                            d1 = fmaf(__ldg(F.out_g + 2 * M + j), wj, d1);
+                        }
+                    } else {
+#pragma unroll 8
+                        for (int i = 0; i < kJ; ++i) {
+                            const int j = t + i * TPS;
+                            d0 = fmaf(__ldg(F.out_g + j), wb[far_phys(j)], d0);
+                        }
                     }
                 }
                 constexpr int width = TPS < 32 ? TPS : 32;
