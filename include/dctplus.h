@@ -184,9 +184,17 @@ dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const v
  *   y_dev : batch rows, row stride ldy >= count * n; plan k's coefficients at
  *           columns k n .. k n + n - 1 (ascending eigenvalue). Must not
  *           overlap x.
- * Results equal those of dctplus_execute per plan. Asynchronous on `stream`;
- * uses the plans' stream workspaces (plan 0's holds the shared s), so calls
- * that share a plan and a stream must not overlap.
+ * Results equal those of dctplus_execute per plan. Asynchronous on `stream`:
+ * the plans' own products are independent, so within each group of four the
+ * plans after the first run on side streams that the library forks from
+ * `stream` (an event after the work it holds) and joins back into it (the
+ * call returns with `stream` waiting on all of them). The side streams (three
+ * per device and caller stream) are created by the first call on `stream`;
+ * make that call before capturing `stream` into a CUDA graph (a call captured
+ * before it runs the plans one after another on `stream`). Scratch: the
+ * hierarchical and dense sets use the plans' workspaces of `stream` (plan 0's
+ * holds the shared s); plan by plan, each plan uses its workspace of the
+ * stream it runs on. Calls that share a plan and a stream must not overlap.
  * Errors: INVALID_ARG (null or mixed plans, count < 1, strides too small,
  * misaligned or overlapping buffers), the errors of dctplus_execute. */
 dctplus_status dctplus_execute_multi(const dctplus_plan_t* plans, int count, const float* x_dev, int64_t ldx,

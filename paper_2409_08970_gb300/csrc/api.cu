@@ -216,6 +216,45 @@ void note_launch(cudaStream_t s, const char* name, double bytes, double flops) {
     g_trace.push_back({name, bytes, flops, e});
 }
 
+struct SideSet {
+    int dev;
+    cudaStream_t caller;
+    SideStreams s;
+};
+static std::mutex g_side_mu;
+static std::vector<SideSet*> g_side;  // kept until exit: a graph captured on the caller's stream may hold them
+
+const SideStreams* side_streams(int dev, cudaStream_t caller) {
+    {
+        // the kernel trace times the launches one after another on the traced stream
+        std::lock_guard<std::mutex> lk(g_trace_mu);
+        if (g_trace_on && caller == g_trace_stream) return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    for (SideSet* e : g_side)
+        if (e->dev == dev && e->caller == caller) return &e->s;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(caller, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    SideSet* e = new (std::nothrow) SideSet{dev, caller, {}};
+    if (!e) return nullptr;
+    bool ok = cudaEventCreateWithFlags(&e->s.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kFarMaxPlans - 1 && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&e->s.side[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e->s.join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (e->s.fork) cudaEventDestroy(e->s.fork);
+        for (int k = 0; k < kFarMaxPlans - 1; ++k) {
+            if (e->s.side[k]) cudaStreamDestroy(e->s.side[k]);
+            if (e->s.join[k]) cudaEventDestroy(e->s.join[k]);
+        }
+        delete e;
+        return nullptr;
+    }
+    g_side.push_back(e);
+    return &e->s;
+}
+
 }  // namespace dctplus
 
 using namespace dctplus;
@@ -443,22 +482,27 @@ dctplus_status dctplus_execute_multi(const dctplus_plan_t* plans, int count, con
         }
         return DCTPLUS_OK;
     }
+    const int dev = plans[0]->device;
     if (all_dense && y_ok) {
-        // one DCT-II, then each plan's dense product from the same s
+        // one DCT-II, then each plan's dense product from the same s (up to four at a time)
         float* ws = static_cast<float*>(plan_workspace(plans[0], s, sizeof(float) * (size_t)batch * n));
         if (!ws) return DCTPLUS_ERR_CUDA;
         if ((st = launch_dct_fft(plans[0], x_dev, ldx, ws, n, batch, s)) != DCTPLUS_OK) return st;
-        for (int k = 0; k < count; ++k)
-            if ((st = launch_gemm_tc(ws, nullptr, n, plans[k]->d_whi, plans[k]->d_wlo, n, y_dev + (int64_t)k * n, ldy,
-                                     (int)batch, n, n, s, plans[k]->device)) != DCTPLUS_OK)
-                return st;
-        return DCTPLUS_OK;
+        for (int k0 = 0; k0 < count && st == DCTPLUS_OK; k0 += kFarMaxPlans)
+            st = run_forked(dev, s, std::min(kFarMaxPlans, count - k0), [&](int k, cudaStream_t sk) {
+                const dctplus_plan_t p = plans[k0 + k];
+                return launch_gemm_tc(ws, nullptr, n, p->d_whi, p->d_wlo, n, y_dev + (int64_t)(k0 + k) * n, ldy,
+                                      (int)batch, n, n, sk, dev);
+            });
+        return st;
     }
-    for (int k = 0; k < count; ++k)
-        if ((st = dctplus_execute(plans[k], DCTPLUS_F32, x_dev, ldx, y_dev + (int64_t)k * n, ldy, batch, stream)) !=
-            DCTPLUS_OK)
-            return st;
-    return DCTPLUS_OK;
+    // plan by plan, up to four at a time (each on its own stream's workspace)
+    for (int k0 = 0; k0 < count && st == DCTPLUS_OK; k0 += kFarMaxPlans)
+        st = run_forked(dev, s, std::min(kFarMaxPlans, count - k0), [&](int k, cudaStream_t sk) {
+            return dctplus_execute(plans[k0 + k], DCTPLUS_F32, x_dev, ldx, y_dev + (int64_t)(k0 + k) * n, ldy,
+                                   batch, reinterpret_cast<dctplus_stream_t>(sk));
+        });
+    return st;
 }
 
 dctplus_status dctplus_execute_host(dctplus_plan_t p, dctplus_dtype dtype, const void* x_host,

@@ -738,8 +738,13 @@ dctplus_status launch_hier_multi(const dctplus_plan_t* plans, int K, const float
         set.f[k] = runs[k].far;
     }
     dctplus_status r = launch_dct_far_multi(plans[0], x, ldx, s_hi, n, batch, set, st);
-    for (int k = 0; k < K && r == DCTPLUS_OK; ++k) r = hier_finish(plans[k], runs[k], s_hi, ys[k], ldy, batch, st);
-    return r;
+    if (r != DCTPLUS_OK) return r;
+    // The plans' far fields and output products depend on the shared DCT only: the plans after
+    // the first run on side streams, so that their products fill the SMs the others leave idle
+    // (a leaf-to-leaf product of fewer tiles than SMs, the last wave of an output product).
+    return run_forked(plans[0]->device, st, K, [&](int k, cudaStream_t sk) {
+        return hier_finish(plans[k], runs[k], s_hi, ys[k], ldy, batch, sk);
+    });
 }
 
 }  // namespace dctplus

@@ -234,6 +234,43 @@ struct DctFarSet {
     DctFar f[kFarMaxPlans];
 };
 
+// api.cu: streams on which plans 1 .. K - 1 of a multi-plan call run their own products, forked
+// from the caller's stream after the shared DCT-II (event `fork`) and joined back (`join`).
+// One set per (device, caller stream), created on first use outside stream capture; null while
+// the caller's stream is being captured before the set exists, or while it is traced.
+struct SideStreams {
+    cudaStream_t side[kFarMaxPlans - 1];
+    cudaEvent_t fork;
+    cudaEvent_t join[kFarMaxPlans - 1];
+};
+const SideStreams* side_streams(int dev, cudaStream_t caller);
+
+// Runs body(k, stream) for k = 0 .. K - 1 (K <= kFarMaxPlans) where the K bodies are independent:
+// body 0 on the caller's stream, the others on side streams forked from it (after the work it
+// already holds) and joined back, also after an error, so that a stream capture stays whole. All
+// on the caller's stream when side_streams gives none.
+template <class Body>
+dctplus_status run_forked(int dev, cudaStream_t st, int K, Body body) {
+    const SideStreams* ss = K > 1 ? side_streams(dev, st) : nullptr;
+    dctplus_status r = DCTPLUS_OK;
+    if (!ss) {
+        for (int k = 0; k < K && r == DCTPLUS_OK; ++k) r = body(k, st);
+        return r;
+    }
+    if (cudaEventRecord(ss->fork, st) != cudaSuccess) return DCTPLUS_ERR_CUDA;
+    for (int k = 1; k < K; ++k) {
+        cudaStream_t sk = ss->side[k - 1];
+        const dctplus_status rk = cudaStreamWaitEvent(sk, ss->fork, 0) == cudaSuccess ? body(k, sk) : DCTPLUS_ERR_CUDA;
+        if (r == DCTPLUS_OK) r = rk;
+    }
+    const dctplus_status r0 = body(0, st);
+    for (int k = 1; k < K; ++k)
+        if (cudaEventRecord(ss->join[k - 1], ss->side[k - 1]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, ss->join[k - 1], 0) != cudaSuccess)
+            r = DCTPLUS_ERR_CUDA;
+    return r != DCTPLUS_OK ? r : r0;
+}
+
 // large.cu
 // DCT-II with the far-field outputs above (n a power of two in [256, 16384])
 dctplus_status launch_dct_far(dctplus_plan_t p, const float* x, int64_t ldx, float* s_out, int64_t lds,

@@ -304,3 +304,39 @@ def test_execute_multi_groups_mixed_sets_and_errors(pkg):
     for p in plans + mixed[1:] + [other]:
         p.close()
     assert pkg.dctplus_sync_check(0) == 0
+
+
+@pytest.mark.parametrize("far_field", [1, 2])
+def test_execute_multi_in_a_cuda_graph(pkg, far_field):
+    """The plans after the first run their products on side streams forked from the caller's
+    stream; captured into a CUDA graph (after a first call on that stream, which sizes the
+    workspaces and creates the side streams), the replays give the plan-by-plan results on
+    fresh inputs."""
+    n, batch = 1024, 300
+    plans = [pkg.Plan(n, random_unit_v(n, seed=8), r, cauchy_mode=pkg.CAUCHY_HIER, far_field=far_field)
+             for r in (-0.3, 2.0, 0.6)]
+    x = torch.tensor(normal_signals(batch, n, seed=21), dtype=torch.float32, device="cuda")
+    y = torch.zeros((batch, 3 * n), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    handles = [p.handle for p in plans]
+    with torch.cuda.stream(stream):
+        pkg.dctplus_execute_multi(handles, x.data_ptr(), n, y.data_ptr(), 3 * n, batch, sh)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        pkg.dctplus_execute_multi(handles, x.data_ptr(), n, y.data_ptr(), 3 * n, batch, sh)
+    for seed in (22, 23):
+        xh = normal_signals(batch, n, seed=seed)
+        x.copy_(torch.tensor(xh, dtype=torch.float32))
+        y.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = y.double().cpu().numpy()
+        for k, p in enumerate(plans):
+            yk = run32(p, xh)
+            assert np.abs(got[:, k * n:(k + 1) * n] - yk).max() <= 1e-6 * np.abs(yk).max(), (seed, k)
+    del g
+    for p in plans:
+        p.close()
+    assert pkg.dctplus_sync_check(0) == 0
