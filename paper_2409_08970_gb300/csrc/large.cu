@@ -130,9 +130,37 @@ __device__ __forceinline__ void dft_reg(float2 (&a)[R]) {
     for (int i = 0; i < R; ++i) a[i] = t[i];
 }
 
-// Shared-memory index of point i of a signal's buffer: one pad slot every 8
-// points keeps the strided accesses of every pass free of bank conflicts.
-__device__ __forceinline__ int fft_phys(int i) { return i + (i >> 3); }
+// Shared-memory index of point i of a signal's FFT buffer: i + sum_s (i >> s), one
+// pad slot every 2^s points for each shift s of the length. The shifts were chosen
+// per length by counting the bank wavefronts of every access the kernels make to the
+// buffer (each pass's strided reads and writes, the Makhoul load, the post-twiddle's
+// digit-reversed reads and the inverse kernel's accesses, 16 lanes of 8 bytes per
+// wavefront): the post-twiddle reads X in the passes' digit-reversed order, so with a
+// single pad every 8 points consecutive k land on one bank pair (16-way at M = 8192).
+// The chosen shifts cut those wavefronts 1.5x (M = 512) to 3.2x (M = 8192) in that count.
+template <int M>
+struct FftPad {
+    static constexpr int s0 = 3, s1 = 0, s2 = 0;  // 0: unused
+};
+template <> struct FftPad<128> { static constexpr int s0 = 4, s1 = 6, s2 = 0; };
+template <> struct FftPad<256> { static constexpr int s0 = 4, s1 = 6, s2 = 0; };
+template <> struct FftPad<512> { static constexpr int s0 = 4, s1 = 7, s2 = 0; };
+template <> struct FftPad<1024> { static constexpr int s0 = 4, s1 = 6, s2 = 0; };
+template <> struct FftPad<2048> { static constexpr int s0 = 4, s1 = 6, s2 = 10; };
+template <> struct FftPad<4096> { static constexpr int s0 = 4, s1 = 9, s2 = 10; };
+template <> struct FftPad<8192> { static constexpr int s0 = 4, s1 = 10, s2 = 0; };
+
+template <int M>
+__host__ __device__ constexpr int fft_phys(int i) {
+    using P = FftPad<M>;
+    return i + (i >> P::s0) + (P::s1 ? (i >> P::s1) : 0) + (P::s2 ? (i >> P::s2) : 0);
+}
+
+// float2 slots of one signal's FFT buffer (even, so that every signal's buffer starts
+// on a 16-byte boundary)
+template <int M>
+__host__ __device__ constexpr int fft_buf() { return (fft_phys<M>(M - 1) + 2) & ~1; }
+static_assert(fft_buf<64>() == 72 && fft_buf<8192>() == 8710, "FFT buffer sizes");
 
 __host__ __device__ constexpr int fft_tw_offset(int M, int B) {
     int off = 0;
@@ -157,14 +185,14 @@ __device__ __forceinline__ void fft_pass(float2* buf, int t, const float2* __res
         const int u = t + j * TPS, b = u / S, n1 = u % S, base = b * B + n1;
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = buf[fft_phys(base + r * S)];
+        for (int r = 0; r < R; ++r) v[r] = buf[fft_phys<M>(base + r * S)];
         dft_reg<R>(v);
         if (S > 1) {
 #pragma unroll
             for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], __ldg(tw + k2 * S + n1));
         }
 #pragma unroll
-        for (int k2 = 0; k2 < R; ++k2) buf[fft_phys(base + k2 * S)] = v[k2];
+        for (int k2 = 0; k2 < R; ++k2) buf[fft_phys<M>(base + k2 * S)] = v[k2];
     }
     __syncthreads();
     if constexpr (S > 1) fft_pass<M, S>(buf, t, twp);
@@ -201,8 +229,8 @@ __device__ __forceinline__ void dct_load(float2* buf, const float* xs, int t, in
 #pragma unroll
     for (int i = 0; i < kLoads; ++i) {
         const int q = t + i * TPS;
-        buf[fft_phys(q)] = make_float2(v[i].x, v[i].z);
-        buf[fft_phys(M - 1 - q)] = make_float2(v[i].w, v[i].y);
+        buf[fft_phys<M>(q)] = make_float2(v[i].x, v[i].z);
+        buf[fft_phys<M>(M - 1 - q)] = make_float2(v[i].w, v[i].y);
     }
 }
 
@@ -212,8 +240,8 @@ __device__ __forceinline__ void dct_load(float2* buf, const float* xs, int t, in
 template <int M>
 __device__ __forceinline__ void dct_post(const float2* buf, int k, const float2* __restrict__ tw_split,
                                          const float2* __restrict__ tw_post, float2& bk, float2& bp) {
-    const float2 xk = buf[fft_phys(fft_out_pos<M>(k))];
-    const float2 xm = buf[fft_phys(fft_out_pos<M>((M - k) & (M - 1)))];
+    const float2 xk = buf[fft_phys<M>(fft_out_pos<M>(k))];
+    const float2 xm = buf[fft_phys<M>(fft_out_pos<M>((M - k) & (M - 1)))];
     const float2 fe = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
     const float2 fo = make_float2(0.5f * (xk.y + xm.y), -0.5f * (xk.x - xm.x));  // (xk - conj xm) / 2i
     float2 tt = cmul(__ldg(tw_split + k), fo);
@@ -233,7 +261,7 @@ __global__ void __launch_bounds__(512) k_dct_r8(int n, const float* __restrict__
                                                 float* __restrict__ s, int64_t lds, int64_t batch,
                                                 const float2* __restrict__ tw, int vec) {
     constexpr int TPS = fft_tps(M);
-    constexpr int BUF = M + M / 8;  // float2 per signal
+    constexpr int BUF = fft_buf<M>();  // float2 per signal
     extern __shared__ __align__(16) float2 dsm[];
     const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
     const int spc = blockDim.x / TPS;
@@ -274,7 +302,7 @@ __global__ void __launch_bounds__(512) k_dct_r8(int n, const float* __restrict__
 template <int M>
 static void r8_shape(int64_t batch, int dev, int* spc_out, size_t* smem_out, int64_t* grid_out) {
     constexpr int TPS = fft_tps(M);
-    constexpr size_t kBufBytes = sizeof(float2) * (M + M / 8);
+    constexpr size_t kBufBytes = sizeof(float2) * fft_buf<M>();
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     sms = std::max(sms, 1);
@@ -340,7 +368,7 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                                                  float* __restrict__ s, int64_t lds, int64_t batch,
                                                  const float2* __restrict__ tw, int vec, const DctFarSet S) {
     constexpr int TPS = fft_tps(M);
-    constexpr int BUF = M + M / 8;
+    constexpr int BUF = fft_buf<M>();
     constexpr int WB = 2 * M + M / 8;  // floats of a signal's w buffer (far_phys(n - 1) < WB)
     constexpr int NLEAF = M / 32;      // n / 64
     constexpr int kPost = (M / 2 + TPS) / TPS;
@@ -583,7 +611,7 @@ static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_ou
         spc = 32 / TPS;
         grid = std::min<int64_t>(grid, (batch + spc - 1) / spc);
     }
-    smem = (size_t)spc * sizeof(float2) * (M + M / 8) +
+    smem = (size_t)spc * sizeof(float2) * fft_buf<M>() +
            sizeof(float) * ((far_alias(M) ? 0 : (size_t)spc * (2 * M + M / 8)) + 2 * 64 * kFarTqLd +
                             2 * 24 * kFarTqLd + spc * kWps * 2);
     static bool attr[64] = {};
@@ -643,7 +671,7 @@ __global__ void __launch_bounds__(512) k_idct_r8(int n, const float* __restrict_
                                                  float* __restrict__ x, int64_t ldx, int64_t batch,
                                                  const float2* __restrict__ tw, int vec) {
     constexpr int TPS = fft_tps(M);
-    constexpr int BUF = M + M / 8;
+    constexpr int BUF = fft_buf<M>();
     extern __shared__ __align__(16) float2 dsm[];
     const int slot = threadIdx.x / TPS, t = threadIdx.x % TPS;
     const int spc = blockDim.x / TPS;
@@ -676,12 +704,12 @@ __global__ void __launch_bounds__(512) k_idct_r8(int n, const float* __restrict_
                 const float2 d = make_float2(vk.x - vm.x, vk.y + vm.y);  // vk - conj vm
                 const float2 wk = __ldg(tw_split + k);
                 const float2 fo = cmul(make_float2(0.5f * d.x, 0.5f * d.y), make_float2(wk.x, -wk.y));
-                buf[fft_phys(k)] = make_float2(fe.x - fo.y, -(fe.y + fo.x));  // conj(X_k)
+                buf[fft_phys<M>(k)] = make_float2(fe.x - fo.y, -(fe.y + fo.x));  // conj(X_k)
                 if (kp != k && kp < M) {
                     const float2 wm = __ldg(tw_split + kp);
                     // fe' = conj fe, fo' = -conj(d) exp(2 pi i kp / n) / 2
                     const float2 fo2 = cmul(make_float2(-0.5f * d.x, 0.5f * d.y), make_float2(wm.x, -wm.y));
-                    buf[fft_phys(kp)] = make_float2(fe.x - fo2.y, -(-fe.y + fo2.x));
+                    buf[fft_phys<M>(kp)] = make_float2(fe.x - fo2.y, -(-fe.y + fo2.x));
                 }
             }
         }
@@ -694,8 +722,8 @@ __global__ void __launch_bounds__(512) k_idct_r8(int n, const float* __restrict_
 #pragma unroll
         for (int i = 0; i < kStores; ++i) {
             const int q = t + i * TPS;
-            const float2 a = buf[fft_phys(fft_out_pos<M>(q))];           // w = conj(buf) / M
-            const float2 b2 = buf[fft_phys(fft_out_pos<M>(M - 1 - q))];
+            const float2 a = buf[fft_phys<M>(fft_out_pos<M>(q))];           // w = conj(buf) / M
+            const float2 b2 = buf[fft_phys<M>(fft_out_pos<M>(M - 1 - q))];
             const float4 v = make_float4(a.x * inv, -b2.y * inv, -a.y * inv, b2.x * inv);
             if (vec) {
                 reinterpret_cast<float4*>(xs)[q] = v;
