@@ -52,7 +52,7 @@ def oracle_rows(n, v, rho, x, rng):
 
 
 # n = 8192 and 16384 have no stored W table: the Cauchy product then generates W tile by
-# tile on the CUDA cores, and n = 16384 runs the DCT with 512 threads and 72 KB of shared memory per signal
+# tile on the CUDA cores, and n = 16384 runs the DCT with 512 threads and 70 KB of shared memory per signal
 @pytest.mark.parametrize("n,batch", [(128, 300), (1024, 4096), (4096, 64), (8192, 512), (16384, 256)])
 def test_noalloc_matches_execute_twice(pkg, n, batch):
     assert batch * n <= MAX_SAMPLES
