@@ -463,7 +463,8 @@ def bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, er
     samples = 2 * batch * n
     out = {"workload": f"n={n}, batch {batch}, x~N(0,1), dense unit v (seed 1), rho in {{-0.3, 2.0}}; "
                        "one step = both plans over the batch in one dctplus_execute_multi call (the "
-                       "hierarchical and dense modes share the DCT-II; the others run plan by plan)"}
+                       "hierarchical and dense modes share the DCT-II, the hierarchical mode also the far "
+                       "field of the common v; the others run plan by plan)"}
     for mode in modes:
         mode, far = mode if isinstance(mode, tuple) else (mode, 0)
         try:
@@ -506,6 +507,25 @@ def bench_large(pkg, torch, dev, stream, args, flush, peaks, n, batch, modes, er
         out[name] = entry
         for p in plans:
             p.close()
+    # one update per step (rho = 2.0, dctplus_execute): nothing shared between updates
+    single = {}
+    for mode, far in ((pkg.CAUCHY_HIER, 1), (pkg.CAUCHY_DENSE_GFT, 0)):
+        try:
+            p1 = pkg.Plan(n, v, 2.0, cauchy_mode=mode, far_field=far)
+        except pkg.DctPlusError:
+            continue
+
+        def step1():
+            pkg.dctplus_execute(p1.handle, pkg.F32, x.data_ptr(), n, y2.data_ptr(), 2 * n, batch, sh)
+
+        t1 = float(np.mean(time_graph(step1, stream, args.steps, args.warmup, flush)[0]))
+        name = MODE_NAMES.get(p1.cauchy_mode, str(mode))
+        if p1.cauchy_mode == pkg.CAUCHY_HIER:
+            name += {1: "_leaf_level", 2: "_tree"}.get(p1.far_field, "")
+        single[name] = {"value": batch * n / (t1 * 1e-3) / 1e9, "unit": "GSamples/s", "ms_per_step": t1}
+        p1.close()
+    if single:
+        out["one_update_per_step"] = single
     if errors and n <= 4096:  # the oracle beside it (rho = 2.0; all coefficients of k signals)
         from oracle import cauchy
         op = oracle_plan(n, v, 2.0)

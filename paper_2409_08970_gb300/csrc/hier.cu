@@ -38,6 +38,7 @@
 // angle; their rows are dense dot products, formed by the DCT kernel from the
 // same z-weighted coefficients and placed after the leaf-local coefficients.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -64,6 +65,8 @@ struct HierTables {
     int nc = 0;                  // leaf-local coefficients nleaf R
     int ncp = 0;                 // nc rounded up to 128 (the leaf-to-leaf product's output width)
     int dslot = 0;               // column of the dense-row slots in the leaf-local array
+    int dbase = 0;               // this plan's first dense-row slot (even): plans that share a
+                                 //   leaf-local array keep their dense rows apart
     int ldl = 0;                 // row pitch of the leaf-local array: dslot + 32
     int ldm = 0;                 // row pitch of the moment (and M2L output) arrays
     int Kx = 0;                  // far-field (L2P) columns per 128-row output tile, multiple of 32
@@ -73,6 +76,8 @@ struct HierTables {
     float* slab_hi = nullptr;    // n x Kw
     float* slab_lo = nullptr;
     float* zf = nullptr;         // n: z_j (0 where deflated)
+    std::vector<float> zf_host;  // the same on the host: plans with equal zf (and form) have the
+                                 //   same moments, far field and leaf-local coefficients
     float* tq_hi = nullptr;      // 64 x kFarTqLd: S_a at the 64 source positions of any leaf
     float* tq_lo = nullptr;
     float* tm_hi = nullptr;      // 24 x kFarTqLd: M2M re-expansion of both children (tree)
@@ -248,6 +253,10 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     h->form = form;
     h->dslot = form == 1 ? h->ncp : h->nc;  // the leaf-to-leaf product writes all ncp columns
     h->ldl = h->dslot + 32;
+    {
+        static std::atomic<unsigned> seq{0};  // plans made one after another get distinct slot pairs
+        h->dbase = 2 * (int)(seq.fetch_add(1) % 16);
+    }
     // L2P weights of each far-field target row against the leaf-local coefficients of
     // its tile's window (leaves lmin .. lmax of the tile, starting at column lmin R)
     int kx = 0;
@@ -259,7 +268,7 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         const int t = r / 128;
         if (row_leaf[r] < 0) {  // dense row o: its value sits in slot o after the leaf window
             for (int o = 0; o < h->nout; ++o)
-                if (h->out_row[o] == r) ext_hi[(size_t)r * kxb + h->Kx + o] = 1.0f;
+                if (h->out_row[o] == r) ext_hi[(size_t)r * kxb + h->Kx + h->dbase + o] = 1.0f;
             continue;
         }
         if (p->row_kind[r] == 0) continue;  // deflated rows have no far field
@@ -443,6 +452,7 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         return cudaMemcpy(*dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice);
     };
     DCTPLUS_CUDA_TRY(up(&h->zf, zf));
+    h->zf_host = zf;
     DCTPLUS_CUDA_TRY(up(&h->tq_hi, tq_hi));
     DCTPLUS_CUDA_TRY(up(&h->tq_lo, tq_lo));
     DCTPLUS_CUDA_TRY(up(&h->ext_hi, ext_hi));
@@ -655,47 +665,77 @@ dctplus_status hier_prepare(dctplus_plan_t p, float* ws, int64_t batch, HierRun*
     far.nout = h->nout;
     far.dv = R->lc + h->dslot;
     far.ldd = h->ldl;
+    far.dbase = h->dbase;
+    far.dzero = 1;
+    far.moments = 1;
     return DCTPLUS_OK;
 }
 
-// Far field (leaf-to-leaf product or the tree's M2L and downward passes) and the output
-// product of one plan, from the shared s.
-dctplus_status hier_finish(dctplus_plan_t p, const HierRun& R, const float* s_hi, float* y, int64_t ldy,
-                           int64_t batch, cudaStream_t st) {
+// A plan whose far-field sources equal those of a plan prepared before it (lead): lead's
+// moments and leaf-local array, into which it writes its dense rows at its own slots.
+void hier_prepare_follower(dctplus_plan_t p, const HierRun& lead, HierRun* R) {
     HierTables* h = p->hier;
-    const int n = p->n;
-    dctplus_status r = DCTPLUS_OK;
+    *R = lead;
+    R->far.out_g = h->out_g;
+    R->far.nout = h->nout;
+    R->far.dbase = h->dbase;
+    R->far.dzero = 0;
+    R->far.moments = 0;
+}
+
+// Plans whose far field is the same: equal length and form, and equal z with the same entries
+// deflated. The moments, the far field and the leaf-local coefficients depend on nothing else:
+// the kernel samples at the Chebyshev nodes, the M2L blocks and the L2L chains are fixed by
+// the length.
+bool same_far_sources(dctplus_plan_t a, dctplus_plan_t b) {
+    const HierTables* ha = a->hier;
+    const HierTables* hb = b->hier;
+    return a->n == b->n && ha->form == hb->form && ha->zf_host.size() == hb->zf_host.size() &&
+           std::memcmp(ha->zf_host.data(), hb->zf_host.data(), sizeof(float) * ha->zf_host.size()) == 0;
+}
+
+// Far field of one plan into its leaf-local array: the leaf-to-leaf product, or the tree's
+// M2L and downward passes.
+dctplus_status hier_far(dctplus_plan_t p, const HierRun& R, int64_t batch, cudaStream_t st) {
+    HierTables* h = p->hier;
     if (h->form != 2) {
         GemmSrc l2l{R.mc, nullptr, h->ldm, h->nc, h->kf_hi, h->kf_lo, h->ncp, h->ncp};
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
         const int64_t wide_tiles = (batch + 127) / 128 * (h->ncp / kGemmBN);
         const int bn = 2 * wide_tiles <= sms ? kL2lNarrow : kGemmBN;
-        r = launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l * (kGemmBN / bn), (double)h->nc, R.lc, nullptr,
-                                h->ldl, (int)batch, h->ncp, st, p->device, "k_gemm_tc", bn);
-        if (r != DCTPLUS_OK) return r;
-    } else {
-        FarTree T;
-        T.m2l = h->m2l;
-        T.slot_box = h->slot_box;
-        T.chain = h->chain;
-        T.nlev = h->nlev;
-        T.nbox = h->nbox;
-        for (int l = 0; l < kFarMaxLev; ++l) {
-            T.lev_off[l] = h->lev_off[l];
-            T.chain_off[l] = h->chain_off[l];
-        }
-        for (int l = 0; l <= kFarMaxLev; ++l) T.box_off[l] = h->box_off[l];
-        const int64_t gy = (batch + kTreeThreads - 1) / kTreeThreads;
-        if (gy > 65535) return DCTPLUS_ERR_UNSUPPORTED;
-        k_far_m2l<<<dim3((unsigned)h->nbox, (unsigned)gy), kTreeThreads, 0, st>>>(T, R.mc, R.vv, h->ldm, batch);
-        note_launch(st, "k_far_m2l", 8.0 * (double)batch * h->ldm, 2.0 * kR * kR * 3.5 * h->nbox * (double)batch);
-        DCTPLUS_CUDA_TRY(cudaGetLastError());
-        k_far_down<<<dim3((unsigned)h->nleaf, (unsigned)gy), kTreeThreads, 0, st>>>(T, R.vv, R.lc, h->ldl, batch);
-        note_launch(st, "k_far_down", 4.0 * (double)batch * (h->ldm + h->nc),
-                    2.0 * kR * kR * (h->nlev - 1) * h->nleaf * (double)batch);
-        DCTPLUS_CUDA_TRY(cudaGetLastError());
+        return launch_gemm_tc_segs(&l2l, 1, h->tab_l2l, h->chunks_l2l * (kGemmBN / bn), (double)h->nc, R.lc,
+                                   nullptr, h->ldl, (int)batch, h->ncp, st, p->device, "k_gemm_tc", bn);
     }
+    FarTree T;
+    T.m2l = h->m2l;
+    T.slot_box = h->slot_box;
+    T.chain = h->chain;
+    T.nlev = h->nlev;
+    T.nbox = h->nbox;
+    for (int l = 0; l < kFarMaxLev; ++l) {
+        T.lev_off[l] = h->lev_off[l];
+        T.chain_off[l] = h->chain_off[l];
+    }
+    for (int l = 0; l <= kFarMaxLev; ++l) T.box_off[l] = h->box_off[l];
+    const int64_t gy = (batch + kTreeThreads - 1) / kTreeThreads;
+    if (gy > 65535) return DCTPLUS_ERR_UNSUPPORTED;
+    k_far_m2l<<<dim3((unsigned)h->nbox, (unsigned)gy), kTreeThreads, 0, st>>>(T, R.mc, R.vv, h->ldm, batch);
+    note_launch(st, "k_far_m2l", 8.0 * (double)batch * h->ldm, 2.0 * kR * kR * 3.5 * h->nbox * (double)batch);
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    k_far_down<<<dim3((unsigned)h->nleaf, (unsigned)gy), kTreeThreads, 0, st>>>(T, R.vv, R.lc, h->ldl, batch);
+    note_launch(st, "k_far_down", 4.0 * (double)batch * (h->ldm + h->nc),
+                2.0 * kR * kR * (h->nlev - 1) * h->nleaf * (double)batch);
+    DCTPLUS_CUDA_TRY(cudaGetLastError());
+    return DCTPLUS_OK;
+}
+
+// The output product of one plan from s and its leaf-local array: near-field band, L2P of
+// the far field and the dense rows.
+dctplus_status hier_out(dctplus_plan_t p, const HierRun& R, const float* s_hi, float* y, int64_t ldy,
+                        int64_t batch, cudaStream_t st) {
+    HierTables* h = p->hier;
+    const int n = p->n;
     GemmSrc out[2] = {{s_hi, nullptr, n, n, h->slab_hi, h->slab_lo, h->Kw, h->Kw},
                       {R.lc, nullptr, h->ldl, h->ldl, h->ext_hi, h->ext_lo, h->Kx + 32, h->Kx + 32}};
     return launch_gemm_tc_segs(out, 2, h->tab_out, h->chunks_out, h->acols_out, y, nullptr, ldy,
@@ -709,9 +749,10 @@ dctplus_status launch_hier(dctplus_plan_t p, const float* x, int64_t ldx, float*
     return launch_hier_multi(&p, 1, x, ldx, &y, ldy, batch, st);
 }
 
-// Several plans of one length over the same signals: one DCT-II (with every plan's moments and
-// dense rows), then each plan's far field and output product into ys[k]. s lives in plan 0's
-// workspace; each plan keeps its own moments and leaf-local coefficients.
+// Several plans of one length over the same signals: one DCT-II (with the moments of every
+// distinct far field and every plan's dense rows), then the far fields and each plan's output
+// product into ys[k]. s lives in plan 0's workspace. Plans that share v (updates that differ
+// in rho only, the progressive case) share z, so their far field is formed once.
 dctplus_status launch_hier_multi(const dctplus_plan_t* plans, int K, const float* x, int64_t ldx,
                                  float* const* ys, int64_t ldy, int64_t batch, cudaStream_t st) {
     if (K < 1 || K > kFarMaxPlans || batch > INT32_MAX || (ldy & 3)) return DCTPLUS_ERR_UNSUPPORTED;
@@ -721,11 +762,30 @@ dctplus_status launch_hier_multi(const dctplus_plan_t* plans, int K, const float
             (reinterpret_cast<uintptr_t>(ys[k]) & 15))
             return DCTPLUS_ERR_UNSUPPORTED;
     if (batch <= 0) return DCTPLUS_OK;
-    HierRun runs[kFarMaxPlans];
-    DctFarSet set;
-    set.K = K;
-    float* s_hi = nullptr;
+    // plans with the same far-field sources share the first one's moments, far field and
+    // leaf-local coefficients (lead[k] = that plan); in the set each lead is followed by the
+    // plans that share its sources
+    int lead[kFarMaxPlans], order[kFarMaxPlans], nset = 0;
+    bool shared = false;
     for (int k = 0; k < K; ++k) {
+        lead[k] = k;
+        for (int j = 0; j < k && lead[k] == k; ++j) {
+            if (lead[j] != j || !same_far_sources(plans[j], plans[k])) continue;
+            bool apart = true;  // its dense-row slots differ from those of every plan in j's group
+            for (int i = 0; i < k; ++i)
+                if (lead[i] == j && plans[i]->hier->dbase == plans[k]->hier->dbase) apart = false;
+            if (apart) lead[k] = j;
+        }
+        shared = shared || lead[k] != k;
+    }
+    for (int k = 0; k < K; ++k)
+        if (lead[k] == k)
+            for (int j = k; j < K; ++j)
+                if (lead[j] == k) order[nset++] = j;
+    HierRun runs[kFarMaxPlans];
+    float* s_hi = nullptr;
+    for (int k = 0; k < K; ++k) {  // leads: plan 0 is one, and its workspace also holds s
+        if (lead[k] != k) continue;
         HierTables* h = plans[k]->hier;
         const size_t plane = k == 0 ? (size_t)batch * n : 0;
         const size_t mplane = (size_t)batch * h->ldm, lplane = (size_t)batch * h->ldl;
@@ -735,15 +795,31 @@ dctplus_status launch_hier_multi(const dctplus_plan_t* plans, int K, const float
         if (k == 0) s_hi = ws;
         dctplus_status r = hier_prepare(plans[k], ws + plane, batch, &runs[k]);
         if (r != DCTPLUS_OK) return r;
-        set.f[k] = runs[k].far;
     }
+    for (int k = 0; k < K; ++k)
+        if (lead[k] != k) hier_prepare_follower(plans[k], runs[lead[k]], &runs[k]);
+    DctFarSet set;
+    set.K = K;
+    for (int i = 0; i < K; ++i) set.f[i] = runs[order[i]].far;
     dctplus_status r = launch_dct_far_multi(plans[0], x, ldx, s_hi, n, batch, set, st);
     if (r != DCTPLUS_OK) return r;
-    // The plans' far fields and output products depend on the shared DCT only: the plans after
-    // the first run on side streams, so that their products fill the SMs the others leave idle
-    // (a leaf-to-leaf product of fewer tiles than SMs, the last wave of an output product).
-    return run_forked(plans[0]->device, st, K, [&](int k, cudaStream_t sk) {
-        return hier_finish(plans[k], runs[k], s_hi, ys[k], ldy, batch, sk);
+    const int dev = plans[0]->device;
+    if (!shared) {
+        // The plans' far fields and output products depend on the shared DCT only: the plans
+        // after the first run on side streams, so that their products fill the SMs the others
+        // leave idle (a leaf-to-leaf product of fewer tiles than SMs, the last wave of an
+        // output product).
+        return run_forked(dev, st, K, [&](int k, cudaStream_t sk) {
+            dctplus_status rk = hier_far(plans[k], runs[k], batch, sk);
+            return rk != DCTPLUS_OK ? rk : hier_out(plans[k], runs[k], s_hi, ys[k], ldy, batch, sk);
+        });
+    }
+    // each distinct far field once into its lead's leaf-local array, which the plans sharing it
+    // read in place (each with its own dense-row slots), then every plan's output product
+    for (int k = 0; k < K; ++k)
+        if (lead[k] == k && (r = hier_far(plans[k], runs[k], batch, st)) != DCTPLUS_OK) return r;
+    return run_forked(dev, st, K, [&](int k, cudaStream_t sk) {
+        return hier_out(plans[k], runs[k], s_hi, ys[k], ldy, batch, sk);
     });
 }
 

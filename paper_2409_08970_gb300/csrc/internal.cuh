@@ -221,9 +221,12 @@ struct DctFar {
     int lev_off[kFarMaxLev];
     const float* out_g;   // nout x n: for the rows whose eigenvalue mu_o lies outside [0, 4],
     int nout;             // g_oj = -a_o / (mu_o - lambda_j) (0 where z_j = 0)
-    float* dv;            // their values dv[b * ldd + o] = sum_j g_oj z_j s_j (slots
-                          // nout .. 31 are written as zeros)
+    float* dv;            // 32 dense-row slots per signal: dv[b * ldd + dbase + o] = sum_j g_oj z_j s_j
     int64_t ldd;
+    int dbase;            // the plan's first slot (even; its nout <= 2 slots follow)
+    int dzero;            // 1: also write zeros to the other slots (the first plan to use dv)
+    int moments;          // 1: form the moments (and M2M); 0: the previous plan of the set
+                          //   has the same zf and formed them (this plan: dense rows only)
 };
 
 // The far-field inputs of up to kFarMaxPlans plans of one length over the same signals: the

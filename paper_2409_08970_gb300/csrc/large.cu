@@ -442,7 +442,9 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
             __syncthreads();
             // n = 2 M: the loops over a signal's coefficients have a fixed trip count, unrolled so
             // that each thread keeps several L2 / L1 loads in flight
-            if (kAlias || kp > 0) {  // w = z s from the s just written (L2)
+            // w = z s from the s just written (L2): every plan at n = 16384, where the moments on
+            // chip may have overwritten w; a plan whose zf differs from the previous plan's otherwise
+            if (kAlias || (kp > 0 && F.moments)) {
                 if (live) {
                     const float* ss = s + sig * lds;
 #pragma unroll 8
@@ -487,7 +489,7 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
             int64_t rsig[2] = {-1, -1};
             int rleaf[2] = {0, 0};
             const int g = lane >> 2, tg = lane & 3;
-            if (warp < ntile) {
+            if (warp < ntile && F.moments) {
                 const float* wrow[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
             }
             // with w over the FFT buffer, the moments may overwrite it only once every warp has read it
             if constexpr (kAlias) __syncthreads();
-            if (warp < ntile) {
+            if (warp < ntile && F.moments) {
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
             __syncthreads();  // the dense rows' partial sums are in red, the leaf moments on chip
             // M2M: level l moments of parent p = E_0 M(left child) + E_1 M(right child), one
             // m16n8k8 row tile of (signal slot, parent) rows per warp, K = 24 (both children)
-            for (int l = 1; l < F.nlev; ++l) {
+            for (int l = 1; F.moments && l < F.nlev; ++l) {
                 const int nb = NLEAF >> l;
                 if (warp < (spc * nb + 15) / 16) {
                     const int g = lane >> 2, tg = lane & 3;
@@ -586,11 +588,15 @@ __global__ void __launch_bounds__(512, 2) k_dct_far(int n, const float* __restri
                 }
                 __syncthreads();
             }
-            if (live) {  // the 32 dense-row slots: values, then zeros
+            if (live) {  // the 32 dense-row slots: this plan's values at its own slots; the first
+                         // plan writing these slots also zeroes the others
                 for (int o = t; o < 32; o += TPS) {
+                    const int q = o - F.dbase;
+                    const bool mine = q >= 0 && q < F.nout;
+                    if (!mine && !F.dzero) continue;
                     float val = 0.f;
-                    if (o < F.nout)
-                        for (int w = 0; w < kWps; ++w) val += red[(slot * kWps + w) * 2 + o];
+                    if (mine)
+                        for (int w = 0; w < kWps; ++w) val += red[(slot * kWps + w) * 2 + q];
                     F.dv[sig * F.ldd + o] = val;
                 }
             }
@@ -622,9 +628,9 @@ static dctplus_status launch_far(int n, const float* x, int64_t ldx, float* s_ou
     }
     k_dct_far<M><<<(unsigned)grid, spc * TPS, smem, st>>>(n, x, ldx, s_out, lds, batch, tw, vec, F);
     double bytes = 8.0 * batch * n, flops = dct_flops(n) * batch;  // the DCT-II, once for the set
-    for (int k = 0; k < F.K; ++k) {  // each plan's moments and dense rows
-        bytes += 4.0 * batch * (n / 64) * kFarR + 4.0 * 32 * batch;
-        flops += 6.0 * kFarR * (double)batch * n + 2.0 * F.f[k].nout * (double)batch * n;
+    for (int k = 0; k < F.K; ++k) {  // each plan's dense rows, and the moments where formed
+        bytes += 4.0 * 32 * batch + (F.f[k].moments ? 4.0 * batch * (n / 64) * kFarR : 0.0);
+        flops += 2.0 * F.f[k].nout * (double)batch * n + (F.f[k].moments ? 6.0 * kFarR * (double)batch * n : 0.0);
     }
     note_launch(st, "k_dct_far", bytes, flops);
     DCTPLUS_CUDA_TRY(cudaGetLastError());

@@ -340,3 +340,26 @@ def test_execute_multi_in_a_cuda_graph(pkg, far_field):
     for p in plans:
         p.close()
     assert pkg.dctplus_sync_check(0) == 0
+
+
+@pytest.mark.parametrize("far_field", [1, 2])
+def test_execute_multi_shared_far_field_and_slot_collisions(pkg, far_field):
+    """Updates that differ in rho only share z, so one far field serves them all; each plan keeps
+    its dense rows in its own pair of slots, taken in turn from sixteen. Seventeen plans made one
+    after another: the first and the last have the same slots and so form their far fields apart,
+    the first two share one. Every block equals the plan's own dctplus_execute."""
+    n = 256
+    v = random_unit_v(n, seed=12)
+    plans = [pkg.Plan(n, v, 0.1 + 0.2 * i, cauchy_mode=pkg.CAUCHY_HIER, far_field=far_field) for i in range(17)]
+    x = normal_signals(140, n, seed=23)
+    for sel in ([0, 1], [0, 16], [0, 16, 1, 2]):
+        chosen = [plans[i] for i in sel]
+        y = run_multi(pkg, chosen, x)
+        for k, p in enumerate(chosen):
+            yk = run32(p, x)
+            assert np.abs(y[:, k * n:(k + 1) * n] - yk).max() <= 1e-6 * np.abs(yk).max(), (sel, k)
+    ref = cauchy.transform(cauchy.make_plan(n, v, 0.1 + 0.2 * 16), x[:16])
+    assert relerr(run_multi(pkg, [plans[0], plans[16]], x)[:16, n:], ref).max() < F32_TOL
+    for p in plans:
+        p.close()
+    assert pkg.dctplus_sync_check(0) == 0
