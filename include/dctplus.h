@@ -179,7 +179,13 @@ dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const v
  * hierarchical mode share it (one DCT per group of up to 4 plans, each plan's
  * far-field inputs formed from the same s), and plans in the dense mode share
  * it before their own products; other sets (and a set listing one plan twice)
- * run plan by plan.
+ * run plan by plan. Hierarchical plans that also share v (updates that differ
+ * in rho only, with the same entries of z deflated) share the source side of
+ * the far field too (Theorem 3.2's expansions depend on z and s alone): its
+ * moments and far-field product are formed once per group and read by every
+ * plan of it. Each plan keeps its dense rows (the rows whose eigenvalue lies
+ * outside [0, 4]) in one of 16 slot pairs taken in turn at plan creation;
+ * plans created 16 apart take the same pair and form their far fields apart.
  *   x_dev : batch rows of n floats, row stride ldx >= n.
  *   y_dev : batch rows, row stride ldy >= count * n; plan k's coefficients at
  *           columns k n .. k n + n - 1 (ascending eigenvalue). Must not
