@@ -195,7 +195,9 @@ dctplus_status dctplus_execute(dctplus_plan_t plan, dctplus_dtype dtype, const v
  * plans after the first run on side streams that the library forks from
  * `stream` (an event after the work it holds) and joins back into it (the
  * call returns with `stream` waiting on all of them). The side streams (three
- * per device and caller stream) are created by the first call on `stream`;
+ * per device and caller stream, kept until the process exits, so a caller
+ * should reuse its streams rather than make one per call) are created by the
+ * first call on `stream`;
  * make that call before capturing `stream` into a CUDA graph (a call captured
  * before it runs the plans one after another on `stream`). Scratch: the
  * hierarchical and dense sets use the plans' workspaces of `stream` (plan 0's
