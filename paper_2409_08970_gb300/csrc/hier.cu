@@ -133,6 +133,32 @@ static double w_entry(int n, int p, double tau, double a, double zj, int j) {
     return -a * zj / (tau - d);
 }
 
+// Leaf-to-leaf kernel samples of the leaf-level far field: entry (I a, J b) is
+// 1 / (mu - lambda) = 1 / (4 sin((ph + th) / 2) sin((ph - th) / 2)) at the Chebyshev node ph of
+// target leaf I and th of source leaf J (node[]), for |I - J| >= 2, split into TF32 hi and
+// remainder (round to nearest even on the bits, as tf32_host); zero for near pairs and for the
+// padding of the nc x nc table to ncp x ncp. FP64, one thread per entry.
+__global__ void k_kf_table(int nleaf, int ncp, const double* __restrict__ node, float* __restrict__ hi,
+                           float* __restrict__ lo) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)ncp * ncp) return;
+    const int ia = (int)(idx / ncp), jb = (int)(idx % ncp);
+    const int nc = nleaf * kR;
+    float h = 0.f, l = 0.f;
+    if (ia < nc && jb < nc && abs(ia / kR - jb / kR) > 1) {
+        const double phi = node[ia], th = node[jb];
+        const double v = 1.0 / (4.0 * sin(0.5 * (phi + th)) * sin(0.5 * (phi - th)));
+        auto rne = [](float f) {
+            const uint32_t u = __float_as_uint(f);
+            return __uint_as_float((u + 0xFFFu + ((u >> 13) & 1u)) & ~0x1FFFu);
+        };
+        h = rne((float)v);
+        l = rne((float)(v - (double)h));
+    }
+    hi[idx] = h;
+    lo[idx] = l;
+}
+
 __global__ void k_band_slab(int n, int Kw, const int* kbeg_tile, const int* row_kind,
                             const int* row_pole, const double* row_tau, const double* row_a,
                             const double* znd, const int* row_leaf, const double* S, float* hi,
@@ -405,29 +431,15 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
     // leaf level: the kernel 1 / (mu - lambda) = 1 / (2 cos th - 2 cos ph) at the
     // Chebyshev nodes of target leaf I (ph) and source leaf J (th), |I - J| >= 2; rows
     // (I, a), columns (J, b), zero-padded to ncp x ncp, and its segment table
-    std::vector<float> kf_hi, kf_lo;
+    // (filled on the device by k_kf_table from the nodes: ncp^2 FP64 entries)
+    std::vector<double> node;
     std::vector<int> tab_l2l;
     if (form == 1) {
         const int nc = h->nc, ncp = h->ncp;
-        kf_hi.assign((size_t)ncp * ncp, 0.0f);
-        kf_lo.assign((size_t)ncp * ncp, 0.0f);
         const double hw = 0.5 * hleaf;
-        std::vector<double> node(nc);
+        node.resize(nc);
         for (int I = 0; I < nleaf; ++I)
             for (int a = 0; a < kR; ++a) node[I * kR + a] = (I + 0.5) * hleaf + hw * cheb_node(a);
-        for (int ia = 0; ia < nc; ++ia) {
-            const int I = ia / kR;
-            const double phi = node[ia];
-            for (int jb = 0; jb < nc; ++jb) {
-                const int J = jb / kR;
-                if (std::abs(I - J) <= 1) continue;
-                const double th = node[jb];
-                const double v = 1.0 / (4.0 * std::sin(0.5 * (phi + th)) * std::sin(0.5 * (phi - th)));
-                const float hi = tf32_host((float)v);
-                kf_hi[(size_t)ia * ncp + jb] = hi;
-                kf_lo[(size_t)ia * ncp + jb] = tf32_host((float)(v - (double)hi));
-            }
-        }
         tab_l2l.assign((size_t)(ncp / kL2lNarrow) * kGemmTabStride, 0);
         for (int t = 0; t < ncp / kL2lNarrow; ++t) {
             int* e = &tab_l2l[(size_t)t * kGemmTabStride];
@@ -465,8 +477,19 @@ dctplus_status setup_hier(dctplus_plan_t p, const double* d_znd) {
         DCTPLUS_CUDA_TRY(up(&h->slot_box, slot_box));
         DCTPLUS_CUDA_TRY(up(&h->chain, chain));
     } else {
-        DCTPLUS_CUDA_TRY(up(&h->kf_hi, kf_hi));
-        DCTPLUS_CUDA_TRY(up(&h->kf_lo, kf_lo));
+        const size_t kf = (size_t)h->ncp * h->ncp;
+        double* d_node = nullptr;
+        DCTPLUS_CUDA_TRY(up(&d_node, node));
+        cudaError_t e = cudaMalloc((void**)&h->kf_hi, sizeof(float) * kf);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h->kf_lo, sizeof(float) * kf);
+        if (e == cudaSuccess) {
+            k_kf_table<<<(unsigned)((kf + 255) / 256), 256>>>(nleaf, h->ncp, d_node, h->kf_hi, h->kf_lo);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(d_node);
+        DCTPLUS_CUDA_TRY(e);
         DCTPLUS_CUDA_TRY(up(&h->tab_l2l, tab_l2l));
     }
     DCTPLUS_CUDA_TRY(up(&h->row_leaf, row_leaf));
