@@ -245,17 +245,20 @@ def run_multi(pkg, plans, x):
     return y.double().cpu().numpy()
 
 
+@pytest.mark.parametrize("count", [2, 3])
 @pytest.mark.parametrize("mode", ["hier_leaf", "hier_tree", "dense"])
 @pytest.mark.parametrize("n", [256, 1024, 4096])
-def test_execute_multi_matches_plan_by_plan(pkg, n, mode):
+def test_execute_multi_matches_plan_by_plan(pkg, n, mode, count):
     """Several updates over the same signals in one call: the hierarchical plans share one DCT-II
     (their moments and dense rows formed from the same s), the dense plans share it before their
-    products. Each plan's block equals its own dctplus_execute, and the first agrees with the
-    Cauchy formula; the batch is ragged for every tile shape."""
+    products. The first two plans have the same v, so their far field is formed once; with two
+    or three plans the sets hold one or two far fields. Each plan's block equals its own
+    dctplus_execute, and the first agrees with the Cauchy formula; the batch is ragged for every
+    tile shape."""
     cm = pkg.CAUCHY_DENSE if mode == "dense" else pkg.CAUCHY_HIER
     far = {"hier_leaf": 1, "hier_tree": 2, "dense": 0}[mode]
     cases = [(random_unit_v(n, seed=3), -0.3), (random_unit_v(n, seed=3), 2.0), (self_loop_v(n, 0), 0.7)]
-    plans = [pkg.Plan(n, v, rho, cauchy_mode=cm, far_field=far) for v, rho in cases]
+    plans = [pkg.Plan(n, v, rho, cauchy_mode=cm, far_field=far) for v, rho in cases[:count]]
     x = normal_signals(150, n, seed=17)
     y = run_multi(pkg, plans, x)
     for k, p in enumerate(plans):
