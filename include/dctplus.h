@@ -263,11 +263,13 @@ dctplus_status dctplus_execute_noalloc(dctplus_plan_t plan, const float* x_dev, 
  *              must not overlap gy or y.
  *   grad_rho : NULL, or one device double (overwritten).
  *   grad_v   : NULL, or n device doubles (overwritten).
- * 2 <= n <= 4096; device pointers 4-byte aligned. The first call for a plan
- * builds its backward tables (W^T and K, 3 x 4 n^2 bytes each; allocates and
- * synchronises, so make it before any stream capture); later calls use the
- * plan's per-stream workspace (4 batch n floats). Asynchronous on `stream`
- * otherwise. Errors: INVALID_ARG, UNSUPPORTED (n > 4096), NO_DEVICE, CUDA. */
+ * 2 <= n <= 16384 (every plan length); device pointers 4-byte aligned. The
+ * first call for a plan builds its backward tables (W^T and K, 3 x 4 n^2 bytes
+ * each, plus U for lengths without an FFT: 1.1 GB each at n = 16384;
+ * allocates and synchronises, so make it before any stream capture); later
+ * calls use the plan's per-stream workspace (4 batch n floats). Asynchronous
+ * on `stream` otherwise. Errors: INVALID_ARG, NO_DEVICE, CUDA (also when the
+ * tables do not fit). */
 dctplus_status dctplus_backward(dctplus_plan_t plan, const float* gy_dev, int64_t ldg,
                                 const float* y_dev, int64_t ldy, float* gx_dev, int64_t ldgx,
                                 double* grad_rho, double* grad_v, int64_t batch,

@@ -31,7 +31,7 @@ dctplus_status launch_gemm_tc(const float* a_hi, const float* a_lo, int64_t lda,
                               int K, cudaStream_t s, int dev);  // gemm_tc.cu
 void* plan_workspace(dctplus_plan_t p, cudaStream_t st, size_t bytes);  // api.cu
 
-constexpr int kBwdMaxN = 4096;
+constexpr int kBwdMaxN = 16384;  // dense n x n tables: 7 x 4 n^2 bytes, 7.5 GB at n = 16384
 
 struct BackwardTables {
     float* wt_hi = nullptr;  // n x n, W^T, TF32 hi / lo
