@@ -15,7 +15,7 @@
 //
 // Tables (built on the first call for a plan, FP64 then split): W^T and K as
 // TF32 hi/lo pairs for the tensor-core GEMM and in FP32 for the CUDA-core
-// path, and U for the DCT-III when no FFT length applies. n <= 4096.
+// path, and U for the DCT-III when no FFT length applies. Every plan length (n <= 16384).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
